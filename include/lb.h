@@ -1,0 +1,215 @@
+/*
+ * lb.h -- C ABI of the GB300 multiscale lattice Boltzmann library (liblbgb.so).
+ *
+ * The library advances a 2-D lattice split into regions that use different discrete
+ * velocity sets: a low-order Gauss-Hermite set (D2Q9) in the less rarefied part and a
+ * high-order one (D2Q36, or D2Q16) near the walls, as in Meng, Zhang & Shan,
+ * "Multiscale lattice Boltzmann approach to modeling gas flows":
+ *   - velocity sets: roots of Hermite polynomials, weights by Eq. (weight), 2-D sets by
+ *     the product rule (Sec. 2.1);
+ *   - collision: BGK towards the second-order Hermite equilibrium Eq. (demoeq), with the
+ *     body force Eq. (demoforce), relaxation time from the local Knudsen number
+ *     (Eq. (KN): collision rate p / mu);
+ *   - space-time scheme: forward Euler plus second-order TVD minmod fluxes (Sec. 3.1);
+ *   - walls: Maxwell diffuse reflection, ghost node = wall node (Sec. 3.2);
+ *   - interface coupling (Sec. 2.2): mode LB_IFACE_PAPER is the paper's virtual
+ *     boundary (interpolated rho, u; non-equilibrium part extrapolated from each set's
+ *     own side); mode LB_IFACE_HERMITE rebuilds a foreign neighbour in the reader's set
+ *     from its Hermite coefficients up to second order (density, momentum and the full
+ *     second moment, so the non-equilibrium stress crosses the interface).
+ *
+ * Units are the paper's nondimensional ones (Eq. (nondime)): lengths in l0, velocities
+ * in sqrt(R T0), time in l0 / sqrt(R T0).
+ *
+ * Conventions shared by every entry point:
+ *   - Node (i, j) has x = i h, y = j h; arrays "[ny][nx]" are row-major with x fastest.
+ *   - Population order inside a set: alpha = iy * n + ix for the n-point 1-D rule,
+ *     abscissae ascending, xi_alpha = (r_ix, r_iy).
+ *   - Pointers marked "host" are ordinary host memory; "device" pointers are CUDA
+ *     device memory of the current device. The caller keeps ownership of everything
+ *     it passes in; inputs are copied before the call returns unless stated.
+ *   - Every call returns an lb_status. Errors are sticky per context: after a CUDA or
+ *     divergence error, further calls on that context return the same status.
+ *     lb_last_error() gives a message for the calling thread's most recent failure.
+ *   - Work is enqueued on the context's stream (lb_opts.stream, NULL = legacy default
+ *     stream) and is asynchronous unless stated. One context is used by one host
+ *     thread at a time.
+ */
+#ifndef LB_H
+#define LB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_INVALID = 1,   /* bad argument, map, set, CFL > 1 or dt / tau > 1 */
+    LB_ERR_NOMEM = 2,     /* the allocator returned NULL */
+    LB_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+    LB_ERR_DIVERGED = 4,  /* a reduction found a NaN / Inf density or velocity */
+    LB_ERR_TIMEOUT = 5    /* a bounded device wait ran out */
+} lb_status;
+
+/* Velocity sets: the number of populations of the product Gauss-Hermite set. */
+enum { LB_D2Q9 = 9, LB_D2Q16 = 16, LB_D2Q36 = 36 };
+
+/* Population storage in device memory. The *_DEV forms store the deviation
+ * d = f / w_alpha - rho0 from the rest state w_alpha rho0; all forms except
+ * LB_STORE_F64 collide in FP32; LB_STORE_F64 computes in FP64. */
+enum {
+    LB_STORE_F64 = 0,
+    LB_STORE_F32 = 1,
+    LB_STORE_F32_DEV = 2,
+    LB_STORE_F16_DEV = 3,
+    LB_STORE_BF16_DEV = 4
+};
+
+enum { LB_IFACE_PAPER = 0, LB_IFACE_HERMITE = 1 };
+
+enum { LB_WALL_PERIODIC = 0, LB_WALL_DIFFUSE = 1, LB_WALL_PRESSURE = 2 };
+
+/* Moment fields for lb_moments (bit mask; fields are written in bit order). */
+enum {
+    LB_M_RHO = 1u << 0,
+    LB_M_UX = 1u << 1,
+    LB_M_UY = 1u << 2,
+    LB_M_PXY = 1u << 3,      /* sum f (xi_x - u_x)(xi_y - u_y) */
+    LB_M_NEQ_XX = 1u << 4,   /* sum (f - f_eq) xi_x xi_x */
+    LB_M_NEQ_XY = 1u << 5,
+    LB_M_NEQ_YY = 1u << 6,
+    LB_M_QX = 1u << 7,       /* (1/2) sum f |xi - u|^2 (xi_x - u_x) */
+    LB_M_QY = 1u << 8,
+    LB_M_ALL = (1u << 9) - 1u
+};
+
+/* Grid: nx x ny nodes, spacing h in both directions (h <= 0: 1/(ny-1) when the
+ * bottom and top are walls, 1/ny when y is periodic). Time step dt > 0 is taken as
+ * given; dt <= 0 means dt = cfl * h / xi_max over the two sets (Sec. 3.1 leaves dt
+ * open). nx >= 4, ny >= 4. */
+typedef struct {
+    int32_t nx, ny;
+    double h;
+    double cfl;
+    double dt;
+} lb_grid;
+
+/* One side of the domain, in the order bottom (y = 0), top (y = (ny-1) h), left
+ * (x = 0), right (x = (nx-1) h).
+ *   LB_WALL_DIFFUSE (bottom / top only): wall node moving at (ux, uy), multiplied by
+ *     sin(omega t) when omega > 0 (oscillating plate, Sec. 3.5).
+ *   LB_WALL_PRESSURE (left / right only): the column is not evolved; it holds
+ *     f_eq(rho, u_inner) + f_neq of the next node inwards.
+ *   LB_WALL_PERIODIC: bottom and top together, left and right together. */
+typedef struct {
+    int32_t kind;
+    double ux, uy;
+    double rho;
+    double omega;
+} lb_wall;
+
+/* Relaxation time tau = kn_ref * rho_ref / rho (rho_ref <= 0: tau = kn_ref), minus
+ * dt / 2 when tau_mode = 1. */
+typedef struct {
+    double kn_ref, rho_ref;
+    int32_t tau_mode;
+} lb_kn;
+
+/* Device memory comes from alloc(bytes, alloc_user) and goes back through
+ * free(ptr, alloc_user) when both are set, else from cudaMalloc / cudaFree.
+ * stream is a cudaStream_t. reduce_every > 0 runs the mass / residual reduction
+ * every that many steps inside lb_step and flags divergence. variant < 0 lets
+ * lb_create time the step-kernel layouts on this lattice and keep the fastest
+ * (cached per process); 0 .. 3 forces one (0: one row per thread; 1, 2, 3: a
+ * register window of 2, 3, 4 rows per thread). All layouts give the same result. */
+typedef struct {
+    int32_t store;
+    int32_t iface;
+    double rho0;
+    double gx, gy;
+    int32_t reduce_every;
+    int32_t variant;
+    void *stream;
+    void *(*alloc)(size_t bytes, void *user);
+    void (*free)(void *ptr, void *user);
+    void *alloc_user;
+} lb_opts;
+
+typedef struct lb_ctx lb_ctx;
+
+/* Creates a lattice.
+ *   region_map: host [ny][nx], 0 = low-order set sets[0], 1 = high-order set sets[1].
+ *     The library quantises it to tiles of 32 columns x 1 row: a tile uses the
+ *     high-order set if any of its nodes asks for it (lb_effective_map returns the
+ *     result). Mode LB_IFACE_PAPER needs every row to use one set across x.
+ *   sets: {low, high} population counts, each 9, 16 or 36.
+ * The state starts at rest: f = w_alpha rho0. */
+int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets[2], const lb_kn *kn,
+              const lb_wall walls[4], const lb_opts *opts, lb_ctx **out);
+
+/* f = f_eq(rho, u) at every node (Eq. (demoeq)), host arrays [ny][nx]; a NULL array
+ * means rho0 (rho) or 0 (ux, uy). Synchronous. */
+int lb_init_equilibrium(lb_ctx *ctx, const double *rho, const double *ux, const double *uy);
+
+/* Advances n time steps (Sec. 3.1 scheme, Sec. 3.2 walls, Sec. 2.2 coupling),
+ * asynchronously on the context's stream. */
+int lb_step(lb_ctx *ctx, int64_t n);
+
+/* Moment fields of the current level into dst, laid out [k][ny][nx] for the k-th set
+ * bit of mask, as float (dst_f64 = 0) or double. dst is device memory when
+ * dst_is_device != 0 (asynchronous), else host memory (synchronous). */
+int lb_moments(lb_ctx *ctx, uint32_t mask, void *dst, int32_t dst_is_device, int32_t dst_f64);
+
+/* Runs the reduction on the current level now and returns, synchronously,
+ * out[0] = total mass sum rho (FP64), out[1] = residual ||u - u_prev|| / ||u|| against
+ * the previous reduction (1 on the first call, which compares with u = 0),
+ * out[2] = number of non-finite nodes, out[3] = step count. */
+int lb_reductions(lb_ctx *ctx, double out[4]);
+
+/* The tile-quantised map actually run, host [ny][nx] (0 / 1). */
+int lb_effective_map(lb_ctx *ctx, uint8_t *dst);
+
+/* Replaces the region map; nodes that change set are rebuilt in the new set from
+ * their second-order Hermite coefficients. Synchronous. */
+int lb_set_region_map(lb_ctx *ctx, const uint8_t *region_map);
+
+/* Populations of set s (0 low, 1 high) as stored, decoded to f, host
+ * double [q_s][ny][nx]. Nodes of the other set hold the set-s view that readers of
+ * set s use next to an interface, or unspecified values elsewhere. Synchronous. */
+int lb_get_populations(lb_ctx *ctx, int32_t set, double *dst);
+
+/* Sets the populations of the nodes that use set s from host double [q_s][ny][nx]
+ * (values at other nodes are ignored), then refreshes interface views. Synchronous. */
+int lb_set_populations(lb_ctx *ctx, int32_t set, const double *src);
+
+/* Raw state (both sets, current level, storage format) for checkpoints and
+ * host-resident pipelines: lb_state_bytes gives the size; load / store copy it from /
+ * to host memory on the context's stream (synchronous). */
+int lb_state_bytes(lb_ctx *ctx, size_t *bytes);
+int lb_state_load(lb_ctx *ctx, const void *src, size_t bytes);
+int lb_state_store(lb_ctx *ctx, void *dst, size_t bytes);
+
+/* Checkpoint file: header (grid, sets, storage, step, time) + raw state. */
+int lb_save(lb_ctx *ctx, const char *path);
+int lb_load(lb_ctx *ctx, const char *path);
+
+/* dt, h, step count, time of the current level and the step-kernel layout in use
+ * (any pointer may be NULL). */
+int lb_info(lb_ctx *ctx, double *dt, double *h, int64_t *step, double *time, int32_t *variant);
+
+/* Waits for the context's stream; returns the sticky status. */
+int lb_sync(lb_ctx *ctx);
+
+void lb_destroy(lb_ctx *ctx);
+
+/* Message of the calling thread's most recent error ("" if none). */
+const char *lb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_H */

@@ -1,0 +1,351 @@
+"""Python binding of liblbgb.so, the GB300 multiscale lattice Boltzmann library.
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels. The functions below carry the C names of ``include/lb.h``; ``Lattice`` wraps
+one context. Device memory can come from PyTorch's caching allocator
+(``torch_allocator=True``) and work runs on PyTorch's current CUDA stream.
+
+There is no CPU fallback: importing this package raises if the CUDA library has not
+been built (``python -c "import __graft_entry__ as g; g.build()"``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbgb.so")
+
+LB_OK, LB_ERR_INVALID, LB_ERR_NOMEM, LB_ERR_CUDA, LB_ERR_DIVERGED, LB_ERR_TIMEOUT = range(6)
+LB_STORE_F64, LB_STORE_F32, LB_STORE_F32_DEV, LB_STORE_F16_DEV, LB_STORE_BF16_DEV = range(5)
+LB_IFACE_PAPER, LB_IFACE_HERMITE = 0, 1
+LB_WALL_PERIODIC, LB_WALL_DIFFUSE, LB_WALL_PRESSURE = 0, 1, 2
+MOMENT_NAMES = ("rho", "ux", "uy", "pxy", "neq_xx", "neq_xy", "neq_yy", "qx", "qy")
+LB_M_ALL = (1 << 9) - 1
+STORES = {"f64": LB_STORE_F64, "f32": LB_STORE_F32, "f32_dev": LB_STORE_F32_DEV,
+          "f16_dev": LB_STORE_F16_DEV, "bf16_dev": LB_STORE_BF16_DEV}
+STORE_DTYPE = {LB_STORE_F64: "f64", LB_STORE_F32: "f32", LB_STORE_F32_DEV: "f32",
+               LB_STORE_F16_DEV: "f16", LB_STORE_BF16_DEV: "bf16"}
+EXPORTS = ("lb_create", "lb_init_equilibrium", "lb_step", "lb_moments", "lb_reductions", "lb_effective_map",
+           "lb_set_region_map", "lb_get_populations", "lb_set_populations", "lb_state_bytes", "lb_state_load",
+           "lb_state_store", "lb_save", "lb_load", "lb_info", "lb_sync", "lb_destroy", "lb_last_error")
+
+
+class LBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lb status {code}: {msg}")
+        self.code = code
+
+
+class lb_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("h", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("dt", ctypes.c_double)]
+
+
+class lb_wall(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("ux", ctypes.c_double), ("uy", ctypes.c_double),
+                ("rho", ctypes.c_double), ("omega", ctypes.c_double)]
+
+
+class lb_kn(ctypes.Structure):
+    _fields_ = [("kn_ref", ctypes.c_double), ("rho_ref", ctypes.c_double), ("tau_mode", ctypes.c_int32)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class lb_opts(ctypes.Structure):
+    _fields_ = [("store", ctypes.c_int32), ("iface", ctypes.c_int32), ("rho0", ctypes.c_double),
+                ("gx", ctypes.c_double), ("gy", ctypes.c_double), ("reduce_every", ctypes.c_int32),
+                ("variant", ctypes.c_int32),
+                ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_user", ctypes.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first (__graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    L.lb_create.argtypes = [ctypes.POINTER(lb_grid), u8p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(lb_kn),
+                            ctypes.POINTER(lb_wall), ctypes.POINTER(lb_opts), ctypes.POINTER(P)]
+    L.lb_init_equilibrium.argtypes = [P, dp, dp, dp]
+    L.lb_step.argtypes = [P, ctypes.c_int64]
+    L.lb_moments.argtypes = [P, ctypes.c_uint32, P, ctypes.c_int32, ctypes.c_int32]
+    L.lb_reductions.argtypes = [P, dp]
+    L.lb_effective_map.argtypes = [P, u8p]
+    L.lb_set_region_map.argtypes = [P, u8p]
+    L.lb_get_populations.argtypes = [P, ctypes.c_int32, dp]
+    L.lb_set_populations.argtypes = [P, ctypes.c_int32, dp]
+    L.lb_state_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+    L.lb_state_load.argtypes = [P, P, ctypes.c_size_t]
+    L.lb_state_store.argtypes = [P, P, ctypes.c_size_t]
+    L.lb_save.argtypes = [P, ctypes.c_char_p]
+    L.lb_load.argtypes = [P, ctypes.c_char_p]
+    L.lb_info.argtypes = [P, dp, dp, ctypes.POINTER(ctypes.c_int64), dp, ctypes.POINTER(ctypes.c_int32)]
+    L.lb_sync.argtypes = [P]
+    L.lb_destroy.argtypes = [P]
+    L.lb_destroy.restype = None
+    L.lb_last_error.restype = ctypes.c_char_p
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(code):
+    if code != LB_OK:
+        raise LBError(code, _lib.lb_last_error().decode())
+    return code
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ------------------------------------------------------------ C-named calls
+
+def lb_create(grid, region_map, sets, kn, walls, opts):
+    ctx = ctypes.c_void_p()
+    m = np.ascontiguousarray(region_map, dtype=np.uint8)
+    s = (ctypes.c_int32 * 2)(*sets)
+    w = (lb_wall * 4)(*walls)
+    _check(_lib.lb_create(ctypes.byref(grid), m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), s,
+                          ctypes.byref(kn), w, ctypes.byref(opts), ctypes.byref(ctx)))
+    return ctx
+
+
+def lb_init_equilibrium(ctx, rho=None, ux=None, uy=None):
+    arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy)]
+    ptrs = [None if a is None else _dp(a) for a in arrs]
+    _check(_lib.lb_init_equilibrium(ctx, *ptrs))
+
+
+def lb_step(ctx, n):
+    _check(_lib.lb_step(ctx, int(n)))
+
+
+def lb_moments(ctx, mask, dst_ptr, dst_is_device, dst_f64):
+    _check(_lib.lb_moments(ctx, mask, ctypes.c_void_p(dst_ptr), int(dst_is_device), int(dst_f64)))
+
+
+def lb_reductions(ctx):
+    out = np.zeros(4)
+    _check(_lib.lb_reductions(ctx, _dp(out)))
+    return out
+
+
+def lb_effective_map(ctx, nx, ny):
+    out = np.zeros((ny, nx), dtype=np.uint8)
+    _check(_lib.lb_effective_map(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+    return out
+
+
+def lb_set_region_map(ctx, region_map):
+    m = np.ascontiguousarray(region_map, dtype=np.uint8)
+    _check(_lib.lb_set_region_map(ctx, m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+
+
+def lb_get_populations(ctx, s, q, nx, ny):
+    out = np.zeros((q, ny, nx))
+    _check(_lib.lb_get_populations(ctx, int(s), _dp(out)))
+    return out
+
+
+def lb_set_populations(ctx, s, f):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _check(_lib.lb_set_populations(ctx, int(s), _dp(f)))
+
+
+def lb_state_bytes(ctx):
+    n = ctypes.c_size_t()
+    _check(_lib.lb_state_bytes(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def lb_state_load(ctx, ptr, nbytes):
+    _check(_lib.lb_state_load(ctx, ctypes.c_void_p(ptr), ctypes.c_size_t(nbytes)))
+
+
+def lb_state_store(ctx, ptr, nbytes):
+    _check(_lib.lb_state_store(ctx, ctypes.c_void_p(ptr), ctypes.c_size_t(nbytes)))
+
+
+def lb_save(ctx, path):
+    _check(_lib.lb_save(ctx, os.fsencode(path)))
+
+
+def lb_load(ctx, path):
+    _check(_lib.lb_load(ctx, os.fsencode(path)))
+
+
+def lb_info(ctx):
+    dt, h, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    st = ctypes.c_int64()
+    var = ctypes.c_int32()
+    _check(_lib.lb_info(ctx, ctypes.byref(dt), ctypes.byref(h), ctypes.byref(st), ctypes.byref(t), ctypes.byref(var)))
+    return {"dt": dt.value, "h": h.value, "step": st.value, "time": t.value, "variant": var.value}
+
+
+def lb_sync(ctx):
+    return _check(_lib.lb_sync(ctx))
+
+
+def lb_destroy(ctx):
+    _lib.lb_destroy(ctx)
+
+
+def lb_last_error():
+    return _lib.lb_last_error().decode()
+
+
+# ----------------------------------------------------------------- Lattice
+
+_SIDES = ("bottom", "top", "left", "right")
+_KINDS = {"periodic": LB_WALL_PERIODIC, "diffuse": LB_WALL_DIFFUSE, "pressure": LB_WALL_PRESSURE}
+
+
+def _walls(spec):
+    spec = spec or {}
+    out = []
+    for s in _SIDES:
+        d = spec.get(s, {})
+        kind = d.get("kind", "periodic" if s in ("left", "right") else "diffuse")
+        out.append(lb_wall(_KINDS[kind], d.get("ux", 0.0), d.get("uy", 0.0), d.get("rho", 1.0), d.get("omega", 0.0)))
+    return out
+
+
+class _TorchAllocator:
+    """Device memory for the library from PyTorch's caching allocator."""
+
+    def __init__(self, stream):
+        import torch
+        self._torch = torch
+        self._stream = stream
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, user):
+        try:
+            return self._torch.cuda.caching_allocator_alloc(int(nbytes), stream=self._stream)
+        except Exception:   # out of memory: the library reports LB_ERR_NOMEM
+            return None
+
+    def _free(self, ptr, user):
+        self._torch.cuda.caching_allocator_delete(ptr)
+
+
+class Lattice:
+    """One lattice context (see include/lb.h for the meaning of every field)."""
+
+    def __init__(self, nx, ny, region_map, sets=(9, 36), kn_ref=0.1, rho_ref=1.0, tau_mode=0, walls=None,
+                 store="f32", iface="hermite", rho0=1.0, gx=0.0, gy=0.0, cfl=0.5, dt=0.0, h=0.0,
+                 reduce_every=0, stream=None, torch_allocator=True, variant=-1):
+        self.nx, self.ny = int(nx), int(ny)
+        self.sets = tuple(int(s) for s in sets)
+        self.store = STORES[store] if isinstance(store, str) else int(store)
+        self._alloc = None
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream()
+        self._stream_obj = stream
+        sp = getattr(stream, "cuda_stream", stream)
+        opts = lb_opts()
+        opts.store = self.store
+        opts.iface = LB_IFACE_HERMITE if iface == "hermite" else LB_IFACE_PAPER
+        opts.rho0, opts.gx, opts.gy = rho0, gx, gy
+        opts.reduce_every = int(reduce_every)
+        opts.variant = int(variant)
+        opts.stream = sp
+        if torch_allocator:
+            self._alloc = _TorchAllocator(stream)
+            opts.alloc, opts.free = self._alloc.alloc, self._alloc.free
+        self._opts = opts
+        grid = lb_grid(self.nx, self.ny, h, cfl, dt)
+        kn = lb_kn(kn_ref, rho_ref, tau_mode)
+        self.ctx = lb_create(grid, np.asarray(region_map, dtype=np.uint8).reshape(self.ny, self.nx), self.sets, kn,
+                             _walls(walls), opts)
+        info = lb_info(self.ctx)
+        self.dt, self.h = info["dt"], info["h"]
+
+    @classmethod
+    def from_workload(cls, w, store="f32", **kw):
+        args = dict(sets=w.sets, kn_ref=w.kn_ref, rho_ref=w.rho_ref, tau_mode=w.tau_mode, walls=w.walls,
+                    store=store, iface=w.iface, rho0=w.rho0, gx=w.gx, gy=w.gy, cfl=w.cfl)
+        args.update(kw)
+        lat = cls(w.nx, w.ny, w.region_map, **args)
+        if w.init is not None:
+            lat.init_equilibrium(*w.init)
+        return lat
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_equilibrium(self, rho=None, ux=None, uy=None):
+        shape = (self.ny, self.nx)
+        bc = lambda a: None if a is None else np.broadcast_to(np.asarray(a, dtype=np.float64), shape)
+        lb_init_equilibrium(self.ctx, bc(rho), bc(ux), bc(uy))
+
+    def step(self, n=1):
+        lb_step(self.ctx, n)
+
+    def moments(self, mask=LB_M_ALL, f64=True):
+        nf = bin(mask).count("1")
+        out = np.zeros((nf, self.ny, self.nx), dtype=np.float64 if f64 else np.float32)
+        lb_moments(self.ctx, mask, out.ctypes.data, 0, 1 if f64 else 0)
+        names = [n for k, n in enumerate(MOMENT_NAMES) if mask & (1 << k)]
+        return dict(zip(names, out))
+
+    def moments_into(self, tensor, mask=LB_M_ALL):
+        """Asynchronous write of the moment fields into a CUDA tensor [k][ny][nx]."""
+        import torch
+        assert tensor.is_cuda and tensor.is_contiguous() and tensor.dtype in (torch.float32, torch.float64)
+        lb_moments(self.ctx, mask, tensor.data_ptr(), 1, 1 if tensor.dtype == torch.float64 else 0)
+
+    def reductions(self):
+        r = lb_reductions(self.ctx)
+        return {"mass": r[0], "residual": r[1], "nonfinite": r[2], "step": r[3]}
+
+    def effective_map(self):
+        return lb_effective_map(self.ctx, self.nx, self.ny)
+
+    def set_region_map(self, m):
+        lb_set_region_map(self.ctx, np.asarray(m, dtype=np.uint8).reshape(self.ny, self.nx))
+
+    def populations(self, s):
+        return lb_get_populations(self.ctx, s, self.sets[s], self.nx, self.ny)
+
+    def set_populations(self, s, f):
+        lb_set_populations(self.ctx, s, f)
+
+    def state_bytes(self):
+        return lb_state_bytes(self.ctx)
+
+    def save(self, path):
+        lb_save(self.ctx, path)
+
+    def load(self, path):
+        lb_load(self.ctx, path)
+
+    def info(self):
+        return lb_info(self.ctx)
+
+    def sync(self):
+        return lb_sync(self.ctx)

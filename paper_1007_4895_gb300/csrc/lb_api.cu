@@ -1,0 +1,862 @@
+/*
+ * lb_api.cu -- host side of liblbgb.so: the C ABI declared in include/lb.h.
+ *
+ * Holds the lattice description, builds the velocity-set constants and the tile map,
+ * owns the device planes (two time levels per set), and sequences the kernels of one
+ * time step: the fused update, then the mode-A interface rows and the pressure
+ * columns of the new level, then (every reduce_every steps) the FP64 reduction.
+ */
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/lb.h"
+#include "lb_internal.h"
+
+namespace lbq {
+int velocity_set(int q, double *cx, double *cy, double *w);
+}
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
+
+size_t elem_size(int store)
+{
+    switch (store) {
+        case LB_STORE_F64: return 8;
+        case LB_STORE_F32:
+        case LB_STORE_F32_DEV: return 4;
+        default: return 2;
+    }
+}
+
+}  // namespace
+
+struct lb_ctx {
+    int nx = 0, ny = 0, pitch = 0, ntx = 0;
+    double h = 0.0, dt = 0.0;
+    int q[2] = {0, 0};
+    double cx[2][LB_QMAX], cy[2][LB_QMAX], w[2][LB_QMAX];
+    lb_kn kn{};
+    lb_wall walls[4]{};
+    lb_opts opts{};
+    int store = 0;
+    size_t esize = 0;
+    void *planes[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   /* [level][set] */
+    size_t set_bytes[2] = {0, 0};
+    int cur = 0;
+    uint8_t *d_tmap = nullptr;
+    std::vector<uint8_t> tmap;
+    std::vector<int> iface_rows;
+    double *d_part = nullptr, *d_out = nullptr;
+    unsigned int *d_counter = nullptr;
+    void *d_uprev = nullptr;
+    double *h_out = nullptr;        /* pinned */
+    cudaEvent_t red_event = nullptr;
+    bool red_pending = false;
+    int red_blocks = 1;
+    cudaStream_t stream = nullptr;
+    double t = 0.0;
+    int64_t step = 0;
+    int status = LB_OK;
+    int variant = -1;               /* step kernel layout in use (see launch_step2) */
+    std::vector<void *> owned;
+};
+
+namespace {
+
+bool use_f64(const lb_ctx *c) { return c->store == LB_STORE_F64; }
+
+void *dev_alloc(lb_ctx *c, size_t bytes)
+{
+    void *p = nullptr;
+    if (c->opts.alloc && c->opts.free) {
+        p = c->opts.alloc(bytes, c->opts.alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void dev_free(lb_ctx *c, void *p)
+{
+    if (!p) return;
+    if (c->opts.alloc && c->opts.free) c->opts.free(p, c->opts.alloc_user);
+    else cudaFree(p);
+}
+
+int cuda_check(lb_ctx *c, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return LB_OK;
+    c->status = LB_ERR_CUDA;
+    return fail(LB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int launch_check(lb_ctx *c, const char *what) { return cuda_check(c, cudaGetLastError(), what); }
+
+double wall_speed(const lb_wall &wl, double t, int comp)
+{
+    double u = comp == 0 ? wl.ux : wl.uy;
+    if (wl.omega > 0.0) u *= std::sin(wl.omega * t);
+    return u;
+}
+
+template <typename R>
+void fill_set(const lb_ctx *c, int s, SetConst<R> &k)
+{
+    k.q = c->q[s];
+    k.n1d = c->q[s] == 9 ? 3 : c->q[s] == 16 ? 4 : 6;
+    for (int a = 0; a < LB_QMAX; ++a) {
+        const bool on = a < c->q[s];
+        const double x = on ? c->cx[s][a] : 0.0, y = on ? c->cy[s][a] : 0.0, w = on ? c->w[s][a] : 1.0;
+        const double crx = x * c->dt / c->h, cry = y * c->dt / c->h;
+        k.cx[a] = R(x);
+        k.cy[a] = R(y);
+        k.w[a] = R(w);
+        k.winv[a] = R(1.0 / w);
+        k.wcx[a] = R(w * x);
+        k.wcy[a] = R(w * y);
+        k.crx[a] = R(crx);
+        k.cry[a] = R(cry);
+        k.kx[a] = R(0.5 * (1.0 - std::fabs(crx)));
+        k.ky[a] = R(0.5 * (1.0 - std::fabs(cry)));
+        k.wxx[a] = R(w * (x * x - 1.0));
+        k.wxy[a] = R(w * x * y);
+        k.wyy[a] = R(w * (y * y - 1.0));
+        k.hxx[a] = R(0.5 * (x * x - 1.0));
+        k.hxy[a] = R(x * y);
+        k.hyy[a] = R(0.5 * (y * y - 1.0));
+    }
+}
+
+/* Launch parameters; level `in` is read, level `out` written; walls at time t_new. */
+template <typename R>
+StepParams<R> make_params(const lb_ctx *c, int in, int out, double t_new)
+{
+    StepParams<R> p;
+    std::memset(&p, 0, sizeof(p));
+    p.nx = c->nx;
+    p.ny = c->ny;
+    p.pitch = c->pitch;
+    p.ntx = c->ntx;
+    p.tmap = c->d_tmap;
+    for (int s = 0; s < 2; ++s) {
+        p.fin[s] = c->planes[in][s];
+        p.fout[s] = c->planes[out][s];
+    }
+    p.rho0 = R(c->opts.rho0);
+    p.dt = R(c->dt);
+    p.tau_const = c->kn.rho_ref > 0.0 ? 0 : 1;
+    p.kn_rho = R(c->kn.rho_ref > 0.0 ? c->kn.kn_ref * c->kn.rho_ref : c->kn.kn_ref);
+    p.tau_shift = R(c->kn.tau_mode == 1 ? 0.5 * c->dt : 0.0);
+    p.gx = R(c->opts.gx);
+    p.gy = R(c->opts.gy);
+    p.has_force = (c->opts.gx != 0.0 || c->opts.gy != 0.0) ? 1 : 0;
+    p.periodic_x = c->walls[2].kind == LB_WALL_PERIODIC;
+    p.periodic_y = c->walls[0].kind == LB_WALL_PERIODIC;
+    for (int side = 0; side < 2; ++side) {
+        p.wall_diffuse[side] = c->walls[side].kind == LB_WALL_DIFFUSE;
+        p.pressure[side] = c->walls[2 + side].kind == LB_WALL_PRESSURE;
+        p.rho_side[side] = R(c->walls[2 + side].rho);
+        const double ux = wall_speed(c->walls[side], t_new, 0), uy = wall_speed(c->walls[side], t_new, 1);
+        p.uw_x[side] = R(ux);
+        p.uw_y[side] = R(uy);
+        const double nsg = side == 0 ? 1.0 : -1.0;
+        for (int s = 0; s < 2; ++s) {
+            /* kin - kout = -sum_out |xi.n| w (S / w - 1), summed as such (no cancellation) */
+            double kin = 0.0, kout = 0.0, kdiff = 0.0;
+            for (int a = 0; a < c->q[s]; ++a) {
+                const double xn = c->cy[s][a] * nsg;
+                const double ew = c->cx[s][a] * ux + c->cy[s][a] * uy;
+                const double sm1 = ew + 0.5 * (ew * ew - (ux * ux + uy * uy));
+                if (xn < 0.0) kin += -xn * c->w[s][a];
+                if (xn > 0.0) {
+                    kout += xn * c->w[s][a] * (1.0 + sm1);
+                    kdiff -= xn * c->w[s][a] * sm1;
+                }
+            }
+            p.kin[s][side] = R(kin);
+            p.kout[s][side] = R(kout);
+            p.kdiff[s][side] = R(kdiff);
+        }
+    }
+    p.n_iface = (int)c->iface_rows.size();
+    for (int k = 0; k < p.n_iface && k < LB_MAX_IFACE; ++k) p.iface_row[k] = c->iface_rows[k];
+    fill_set(c, 0, p.set[0]);
+    fill_set(c, 1, p.set[1]);
+    return p;
+}
+
+/* Tile flags from a per-node map; mode A rows and validation. */
+int build_tiles(lb_ctx *c, const uint8_t *map, std::vector<uint8_t> &tm, std::vector<int> &rows)
+{
+    const int nx = c->nx, ny = c->ny, ntx = c->ntx;
+    tm.assign((size_t)ny * ntx, 0);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            const uint8_t v = map[(size_t)j * nx + i];
+            if (v > 1) return fail(LB_ERR_INVALID, "region map values must be 0 or 1");
+            if (v) tm[(size_t)j * ntx + i / LB_TILE_X] |= LB_TILE_HIGH;
+        }
+    const bool px = c->walls[2].kind == LB_WALL_PERIODIC, py = c->walls[0].kind == LB_WALL_PERIODIC;
+    auto hi = [&](int tx, int j) -> int {
+        if (py) j = (j % ny + ny) % ny;
+        else if (j < 0 || j >= ny) return -1;
+        if (px) tx = (tx % ntx + ntx) % ntx;
+        else if (tx < 0 || tx >= ntx) return -1;
+        return tm[(size_t)j * ntx + tx] & LB_TILE_HIGH;
+    };
+    rows.clear();
+    if (c->opts.iface == LB_IFACE_HERMITE) {
+        for (int j = 0; j < ny; ++j)
+            for (int tx = 0; tx < ntx; ++tx) {
+                const int s = hi(tx, j);
+                bool sh = false;
+                for (int d = -2; d <= 2; ++d) {
+                    if (d == 0) continue;
+                    const int o = hi(tx, j + d);
+                    if (o >= 0 && o != s) sh = true;
+                }
+                for (int d = -1; d <= 1; d += 2) {
+                    const int o = hi(tx + d, j);
+                    if (o >= 0 && o != s) sh = true;
+                }
+                if (sh) tm[(size_t)j * ntx + tx] |= LB_TILE_SHADOW;
+            }
+        return LB_OK;
+    }
+    /* mode A: x-uniform rows; interface row = low-order row next to a high-order row */
+    if (c->walls[2].kind == LB_WALL_PRESSURE || c->walls[3].kind == LB_WALL_PRESSURE)
+        return fail(LB_ERR_INVALID, "LB_IFACE_PAPER does not combine with pressure columns");
+    std::vector<int> rs(ny);
+    for (int j = 0; j < ny; ++j) {
+        rs[j] = hi(0, j);
+        for (int tx = 1; tx < ntx; ++tx)
+            if (hi(tx, j) != rs[j]) return fail(LB_ERR_INVALID, "LB_IFACE_PAPER needs every row in one set");
+    }
+    for (int j = 0; j < ny; ++j) {
+        if (rs[j] != 0) continue;
+        const int below = (j > 0 || py) ? rs[(j - 1 + ny) % ny] : -1;
+        const int above = (j < ny - 1 || py) ? rs[(j + 1) % ny] : -1;
+        if (below == 1 && above == 1) return fail(LB_ERR_INVALID, "low-order band one row thick");
+        if (below == 1 || above == 1) {
+            const int jl = below == 1 ? j + 1 : j - 1;
+            if (jl < 0 || jl >= ny || rs[jl] != 0) return fail(LB_ERR_INVALID, "interface row without a low-order side");
+            if (j == 0 || j == ny - 1) return fail(LB_ERR_INVALID, "interface row on a wall");
+            rows.push_back(j);
+            for (int tx = 0; tx < ntx; ++tx)
+                tm[(size_t)j * ntx + tx] |= LB_TILE_IFACE | (below == 1 ? LB_TILE_NEAR_H : 0);
+        }
+    }
+    for (size_t a = 0; a < rows.size(); ++a)
+        for (size_t b = a + 1; b < rows.size(); ++b)
+            if (std::abs(rows[a] - rows[b]) < 4) return fail(LB_ERR_INVALID, "interface rows closer than 4 rows");
+    for (int r : rows) {
+        const int jl = (tm[(size_t)r * ntx] & LB_TILE_NEAR_H) ? r + 1 : r - 1;
+        for (int r2 : rows)
+            if (jl == r2) return fail(LB_ERR_INVALID, "interface rows share a neighbour");
+    }
+    if ((int)rows.size() > LB_MAX_IFACE) return fail(LB_ERR_INVALID, "too many interface rows");
+    return LB_OK;
+}
+
+template <typename R>
+int finalize_level_t(lb_ctx *c, int level)
+{
+    StepParams<R> p = make_params<R>(c, level, level, c->t);
+    void *st = c->stream;
+    if (c->opts.iface == LB_IFACE_HERMITE) lbk::launch_shadows<R>(c->store, p, st);
+    lbk::launch_iface<R>(c->store, p, st);
+    lbk::launch_pressure<R>(c->store, p, st);
+    return launch_check(c, "finalize");
+}
+
+int finalize_level(lb_ctx *c, int level)
+{
+    return use_f64(c) ? finalize_level_t<double>(c, level) : finalize_level_t<float>(c, level);
+}
+
+int upload_tiles(lb_ctx *c)
+{
+    return cuda_check(c, cudaMemcpyAsync(c->d_tmap, c->tmap.data(), c->tmap.size(), cudaMemcpyHostToDevice, c->stream),
+                      "tile map upload");
+}
+
+template <typename R>
+void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
+{
+    if (variant <= 0) lbk::launch_step<R>(c->store, p, c->stream);
+    else lbk::launch_step2<R>(c->store, variant, p, c->stream);
+}
+
+/* Autotuner: times every step-kernel layout on this lattice (reading the current level,
+ * writing the other one, which the next step overwrites) and keeps the fastest. Results
+ * are cached per (storage, grid, sets, interface mode, map) for the process. */
+using TuneKey = std::tuple<int, int, int, int, int, int, uint64_t>;
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+
+template <typename R>
+int autotune_t(lb_ctx *c)
+{
+    uint64_t hsh = 1469598103934665603ull;
+    for (uint8_t b : c->tmap) hsh = (hsh ^ b) * 1099511628211ull;
+    TuneKey key{c->store, c->nx, c->ny, c->q[0], c->q[1], c->opts.iface, hsh};
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) return it->second;
+    }
+    const int nvar = use_f64(c) ? 2 : LB_NUM_VARIANTS;
+    StepParams<R> p = make_params<R>(c, c->cur, c->cur ^ 1, c->t + c->dt);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    int best = 1;
+    float best_ms = 1e30f;
+    for (int v = 0; v < nvar; ++v) {
+        for (int k = 0; k < 2; ++k) launch_variant<R>(c, v, p);
+        cudaEventRecord(e0, c->stream);
+        for (int k = 0; k < 5; ++k) launch_variant<R>(c, v, p);
+        cudaEventRecord(e1, c->stream);
+        float ms = 0.0f;
+        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess) return 1;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[key] = best;
+    return best;
+}
+
+int choose_variant(lb_ctx *c)
+{
+    if (c->opts.variant >= 0) return c->opts.variant < LB_NUM_VARIANTS ? c->opts.variant : 1;
+    return use_f64(c) ? autotune_t<double>(c) : autotune_t<float>(c);
+}
+
+template <typename R>
+int step_t(lb_ctx *c, int64_t n)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        const double t_new = c->t + c->dt;
+        StepParams<R> p = make_params<R>(c, c->cur, c->cur ^ 1, t_new);
+        launch_variant<R>(c, c->variant, p);
+        lbk::launch_iface<R>(c->store, p, c->stream);
+        lbk::launch_pressure<R>(c->store, p, c->stream);
+        if (int e = launch_check(c, "step")) return e;
+        c->cur ^= 1;
+        c->t = t_new;
+        c->step += 1;
+        if (c->opts.reduce_every > 0 && c->step % c->opts.reduce_every == 0) {
+            StepParams<R> q = make_params<R>(c, c->cur, c->cur, c->t);
+            lbk::launch_reduce<R>(c->store, q, static_cast<R *>(c->d_uprev), c->d_part, c->d_counter, c->d_out,
+                                  c->red_blocks, c->stream);
+            if (int e = launch_check(c, "reduce")) return e;
+            if (int e = cuda_check(c, cudaMemcpyAsync(c->h_out, c->d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                                                      c->stream), "reduce copy"))
+                return e;
+            cudaEventRecord(c->red_event, c->stream);
+            c->red_pending = true;
+        }
+    }
+    return LB_OK;
+}
+
+void check_reduction(lb_ctx *c)
+{
+    if (!c->red_pending) return;
+    if (cudaEventQuery(c->red_event) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    c->red_pending = false;
+    if (c->h_out[2] > 0.0 || !std::isfinite(c->h_out[0])) {
+        c->status = LB_ERR_DIVERGED;
+        g_err = "non-finite density or velocity found by the reduction";
+    }
+}
+
+int sticky(lb_ctx *c)
+{
+    if (!c) return fail(LB_ERR_INVALID, "null context");
+    if (c->status != LB_OK) {
+        if (g_err.empty()) g_err = "context is in an error state";
+        return c->status;
+    }
+    return LB_OK;
+}
+
+void free_all(lb_ctx *c)
+{
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (void *p : c->owned) dev_free(c, p);
+    c->owned.clear();
+    if (c->h_out) cudaFreeHost(c->h_out);
+    if (c->red_event) cudaEventDestroy(c->red_event);
+}
+
+void *own(lb_ctx *c, size_t bytes)
+{
+    void *p = dev_alloc(c, bytes);
+    if (p) c->owned.push_back(p);
+    return p;
+}
+
+struct TmpBuf {
+    lb_ctx *c;
+    void *p;
+    TmpBuf(lb_ctx *cc, size_t bytes) : c(cc), p(dev_alloc(cc, bytes)) {}
+    ~TmpBuf()
+    {
+        if (p) {
+            cudaStreamSynchronize(c->stream);
+            dev_free(c, p);
+        }
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char *lb_last_error(void) { return g_err.c_str(); }
+
+int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets[2], const lb_kn *kn,
+              const lb_wall walls[4], const lb_opts *opts, lb_ctx **out)
+{
+    g_err.clear();
+    if (!grid || !region_map || !sets || !kn || !walls || !opts || !out) return fail(LB_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (grid->nx < 4 || grid->ny < 4) return fail(LB_ERR_INVALID, "nx and ny must be >= 4");
+    if ((long long)grid->nx * grid->ny > (1LL << 31)) return fail(LB_ERR_INVALID, "grid too large");
+    if (opts->store < LB_STORE_F64 || opts->store > LB_STORE_BF16_DEV) return fail(LB_ERR_INVALID, "unknown storage");
+    if (opts->iface != LB_IFACE_PAPER && opts->iface != LB_IFACE_HERMITE) return fail(LB_ERR_INVALID, "unknown interface mode");
+    if (opts->variant >= LB_NUM_VARIANTS) return fail(LB_ERR_INVALID, "unknown kernel variant");
+    if (!(opts->rho0 > 0.0)) return fail(LB_ERR_INVALID, "rho0 must be positive");
+    for (int k = 0; k < 4; ++k)
+        if (walls[k].kind < LB_WALL_PERIODIC || walls[k].kind > LB_WALL_PRESSURE)
+            return fail(LB_ERR_INVALID, "unknown wall kind");
+    if ((walls[0].kind == LB_WALL_PERIODIC) != (walls[1].kind == LB_WALL_PERIODIC))
+        return fail(LB_ERR_INVALID, "bottom and top must both be periodic or both not");
+    if ((walls[2].kind == LB_WALL_PERIODIC) != (walls[3].kind == LB_WALL_PERIODIC))
+        return fail(LB_ERR_INVALID, "left and right must both be periodic or both not");
+    if (walls[0].kind == LB_WALL_PRESSURE || walls[1].kind == LB_WALL_PRESSURE)
+        return fail(LB_ERR_INVALID, "pressure sides are left / right only");
+    if (walls[2].kind == LB_WALL_DIFFUSE || walls[3].kind == LB_WALL_DIFFUSE)
+        return fail(LB_ERR_INVALID, "diffuse walls are bottom / top only");
+    for (int k = 2; k < 4; ++k)
+        if (walls[k].kind == LB_WALL_PRESSURE && !(walls[k].rho > 0.0))
+            return fail(LB_ERR_INVALID, "pressure side density must be positive");
+    if (!(kn->kn_ref > 0.0)) return fail(LB_ERR_INVALID, "kn_ref must be positive");
+
+    lb_ctx *c = new lb_ctx();
+    c->nx = grid->nx;
+    c->ny = grid->ny;
+    c->kn = *kn;
+    for (int k = 0; k < 4; ++k) c->walls[k] = walls[k];
+    c->opts = *opts;
+    c->store = opts->store;
+    c->esize = elem_size(opts->store);
+    c->stream = static_cast<cudaStream_t>(opts->stream);
+    double xmax = 0.0;
+    for (int s = 0; s < 2; ++s) {
+        c->q[s] = sets[s];
+        if (lbq::velocity_set(sets[s], c->cx[s], c->cy[s], c->w[s]) != sets[s]) {
+            delete c;
+            return fail(LB_ERR_INVALID, "velocity sets must be 9, 16 or 36");
+        }
+        for (int a = 0; a < c->q[s]; ++a) xmax = std::fmax(xmax, std::fabs(c->cx[s][a]));
+    }
+    c->h = grid->h > 0.0 ? grid->h : (walls[0].kind == LB_WALL_PERIODIC ? 1.0 / grid->ny : 1.0 / (grid->ny - 1));
+    c->dt = grid->dt > 0.0 ? grid->dt : grid->cfl * c->h / xmax;
+    if (!(c->dt > 0.0)) {
+        delete c;
+        return fail(LB_ERR_INVALID, "dt must be positive (cfl > 0 or dt > 0)");
+    }
+    if (xmax * c->dt / c->h > 1.0 + 1e-12) {
+        delete c;
+        return fail(LB_ERR_INVALID, "CFL number xi_max dt / h exceeds 1");
+    }
+    double tau0 = (kn->rho_ref > 0.0 ? kn->kn_ref * kn->rho_ref / opts->rho0 : kn->kn_ref) -
+                  (kn->tau_mode == 1 ? 0.5 * c->dt : 0.0);
+    if (!(tau0 > 0.0) || c->dt / tau0 > 1.0) {
+        delete c;
+        return fail(LB_ERR_INVALID, "dt / tau exceeds 1 at rho0");
+    }
+    c->ntx = (c->nx + LB_TILE_X - 1) / LB_TILE_X;
+    c->pitch = (int)round_up((size_t)c->nx + 16, 32);
+    int e = build_tiles(c, region_map, c->tmap, c->iface_rows);
+    if (e) {
+        delete c;
+        return e;
+    }
+    for (int s = 0; s < 2; ++s) c->set_bytes[s] = (size_t)c->q[s] * c->ny * c->pitch * c->esize;
+    for (int lv = 0; lv < 2; ++lv)
+        for (int s = 0; s < 2; ++s) c->planes[lv][s] = own(c, c->set_bytes[s]);
+    c->d_tmap = static_cast<uint8_t *>(own(c, c->tmap.size()));
+    c->red_blocks = lbk::reduce_blocks(c->nx, c->ny);
+    c->d_part = static_cast<double *>(own(c, sizeof(double) * 4 * c->red_blocks));
+    c->d_out = static_cast<double *>(own(c, sizeof(double) * 4));
+    c->d_counter = static_cast<unsigned int *>(own(c, 256));
+    c->d_uprev = own(c, (size_t)c->nx * c->ny * 2 * (use_f64(c) ? 8 : 4));
+    bool ok = c->d_tmap && c->d_part && c->d_out && c->d_counter && c->d_uprev;
+    for (int lv = 0; lv < 2; ++lv)
+        for (int s = 0; s < 2; ++s) ok = ok && c->planes[lv][s];
+    if (!ok) {
+        free_all(c);
+        delete c;
+        return fail(LB_ERR_NOMEM, "device allocation failed");
+    }
+    if (cudaMallocHost(reinterpret_cast<void **>(&c->h_out), 4 * sizeof(double)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->red_event, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return fail(LB_ERR_CUDA, "pinned buffer / event creation failed");
+    }
+    std::memset(c->h_out, 0, 4 * sizeof(double));
+    cudaError_t ce = cudaSuccess;
+    for (int lv = 0; lv < 2 && ce == cudaSuccess; ++lv)
+        for (int s = 0; s < 2 && ce == cudaSuccess; ++s) ce = cudaMemsetAsync(c->planes[lv][s], 0, c->set_bytes[s], c->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(c->d_counter, 0, 256, c->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(c->d_uprev, 0, (size_t)c->nx * c->ny * 2 * (use_f64(c) ? 8 : 4), c->stream);
+    if (ce != cudaSuccess || upload_tiles(c) != LB_OK) {
+        free_all(c);
+        delete c;
+        return fail(LB_ERR_CUDA, std::string("initial fill failed: ") + cudaGetErrorString(ce));
+    }
+    *out = c;
+    e = lb_init_equilibrium(c, nullptr, nullptr, nullptr);
+    if (e) {
+        lb_destroy(c);
+        *out = nullptr;
+        return e;
+    }
+    c->variant = choose_variant(c);
+    if (int e2 = launch_check(c, "autotune")) {
+        lb_destroy(c);
+        *out = nullptr;
+        return e2;
+    }
+    return LB_OK;
+}
+
+int lb_init_equilibrium(lb_ctx *c, const double *rho, const double *ux, const double *uy)
+{
+    if (int e = sticky(c)) return e;
+    const size_t N = (size_t)c->nx * c->ny;
+    std::vector<double> h(3 * N);
+    for (size_t n = 0; n < N; ++n) {
+        h[n] = rho ? rho[n] : c->opts.rho0;
+        h[N + n] = ux ? ux[n] : 0.0;
+        h[2 * N + n] = uy ? uy[n] : 0.0;
+        if (!(h[n] > 0.0) || !std::isfinite(h[N + n]) || !std::isfinite(h[2 * N + n]))
+            return fail(LB_ERR_INVALID, "initial density must be positive and velocities finite");
+    }
+    TmpBuf tmp(c, 3 * N * sizeof(double));
+    if (!tmp.p) return fail(LB_ERR_NOMEM, "device allocation failed");
+    double *d = static_cast<double *>(tmp.p);
+    if (int e = cuda_check(c, cudaMemcpyAsync(d, h.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+                           "upload"))
+        return e;
+    if (use_f64(c)) {
+        StepParams<double> p = make_params<double>(c, c->cur, c->cur, c->t);
+        lbk::launch_init<double>(c->store, p, d, d + N, d + 2 * N, c->stream);
+    } else {
+        StepParams<float> p = make_params<float>(c, c->cur, c->cur, c->t);
+        lbk::launch_init<float>(c->store, p, d, d + N, d + 2 * N, c->stream);
+    }
+    if (int e = launch_check(c, "init")) return e;
+    if (int e = finalize_level(c, c->cur)) return e;
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "init sync");
+}
+
+int lb_step(lb_ctx *c, int64_t n)
+{
+    if (!c) return fail(LB_ERR_INVALID, "null context");
+    check_reduction(c);
+    if (int e = sticky(c)) return e;
+    if (n < 0) return fail(LB_ERR_INVALID, "negative step count");
+    return use_f64(c) ? step_t<double>(c, n) : step_t<float>(c, n);
+}
+
+int lb_moments(lb_ctx *c, uint32_t mask, void *dst, int32_t dst_is_device, int32_t dst_f64)
+{
+    if (int e = sticky(c)) return e;
+    if (!dst || (mask & ~(uint32_t)LB_M_ALL) || mask == 0) return fail(LB_ERR_INVALID, "bad moments request");
+    int nf = 0;
+    for (int m = 0; m < 9; ++m) nf += (mask >> m) & 1u;
+    const size_t bytes = (size_t)nf * c->nx * c->ny * (dst_f64 ? 8 : 4);
+    void *target = dst;
+    TmpBuf tmp(c, dst_is_device ? 0 : bytes);
+    if (!dst_is_device) {
+        if (!tmp.p) return fail(LB_ERR_NOMEM, "device allocation failed");
+        target = tmp.p;
+    }
+    if (use_f64(c)) {
+        StepParams<double> p = make_params<double>(c, c->cur, c->cur, c->t);
+        lbk::launch_moments<double>(c->store, p, mask, target, dst_f64, c->stream);
+    } else {
+        StepParams<float> p = make_params<float>(c, c->cur, c->cur, c->t);
+        lbk::launch_moments<float>(c->store, p, mask, target, dst_f64, c->stream);
+    }
+    if (int e = launch_check(c, "moments")) return e;
+    if (!dst_is_device) {
+        if (int e = cuda_check(c, cudaMemcpyAsync(dst, target, bytes, cudaMemcpyDeviceToHost, c->stream), "moments copy"))
+            return e;
+        return cuda_check(c, cudaStreamSynchronize(c->stream), "moments sync");
+    }
+    return LB_OK;
+}
+
+int lb_reductions(lb_ctx *c, double out[4])
+{
+    if (int e = sticky(c)) return e;
+    if (!out) return fail(LB_ERR_INVALID, "null output");
+    if (use_f64(c)) {
+        StepParams<double> p = make_params<double>(c, c->cur, c->cur, c->t);
+        lbk::launch_reduce<double>(c->store, p, static_cast<double *>(c->d_uprev), c->d_part, c->d_counter, c->d_out,
+                                   c->red_blocks, c->stream);
+    } else {
+        StepParams<float> p = make_params<float>(c, c->cur, c->cur, c->t);
+        lbk::launch_reduce<float>(c->store, p, static_cast<float *>(c->d_uprev), c->d_part, c->d_counter, c->d_out,
+                                  c->red_blocks, c->stream);
+    }
+    if (int e = launch_check(c, "reduce")) return e;
+    if (int e = cuda_check(c, cudaMemcpyAsync(c->h_out, c->d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                           "reduce copy"))
+        return e;
+    if (int e = cuda_check(c, cudaStreamSynchronize(c->stream), "reduce sync")) return e;
+    c->red_pending = false;
+    out[0] = c->h_out[0];
+    out[1] = c->h_out[1];
+    out[2] = c->h_out[2];
+    out[3] = (double)c->step;
+    if (c->h_out[2] > 0.0 || !std::isfinite(c->h_out[0])) {
+        c->status = LB_ERR_DIVERGED;
+        return fail(LB_ERR_DIVERGED, "non-finite density or velocity found by the reduction");
+    }
+    return LB_OK;
+}
+
+int lb_effective_map(lb_ctx *c, uint8_t *dst)
+{
+    if (!c || !dst) return fail(LB_ERR_INVALID, "null argument");
+    for (int j = 0; j < c->ny; ++j)
+        for (int i = 0; i < c->nx; ++i)
+            dst[(size_t)j * c->nx + i] = c->tmap[(size_t)j * c->ntx + i / LB_TILE_X] & LB_TILE_HIGH;
+    return LB_OK;
+}
+
+int lb_set_region_map(lb_ctx *c, const uint8_t *map)
+{
+    if (int e = sticky(c)) return e;
+    if (!map) return fail(LB_ERR_INVALID, "null map");
+    std::vector<uint8_t> tm;
+    std::vector<int> rows;
+    if (int e = build_tiles(c, map, tm, rows)) return e;
+    /* first rebuild every tile that changes set in its new set (shadow pass with the old
+     * sets and only the changing tiles flagged), then install the new map */
+    std::vector<uint8_t> moving(c->tmap.size());
+    for (size_t k = 0; k < tm.size(); ++k)
+        moving[k] = (uint8_t)((c->tmap[k] & LB_TILE_HIGH) |
+                              (((c->tmap[k] ^ tm[k]) & LB_TILE_HIGH) ? LB_TILE_SHADOW : 0));
+    c->tmap = moving;
+    if (int e = upload_tiles(c)) return e;
+    if (use_f64(c)) {
+        StepParams<double> p = make_params<double>(c, c->cur, c->cur, c->t);
+        lbk::launch_shadows<double>(c->store, p, c->stream);
+    } else {
+        StepParams<float> p = make_params<float>(c, c->cur, c->cur, c->t);
+        lbk::launch_shadows<float>(c->store, p, c->stream);
+    }
+    if (int e = launch_check(c, "remap")) return e;
+    c->tmap = tm;
+    c->iface_rows = rows;
+    if (int e = upload_tiles(c)) return e;
+    if (int e = finalize_level(c, c->cur)) return e;
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "remap sync");
+}
+
+int lb_get_populations(lb_ctx *c, int32_t set, double *dst)
+{
+    if (int e = sticky(c)) return e;
+    if (!dst || set < 0 || set > 1) return fail(LB_ERR_INVALID, "bad argument");
+    const size_t bytes = (size_t)c->q[set] * c->nx * c->ny * sizeof(double);
+    TmpBuf tmp(c, bytes);
+    if (!tmp.p) return fail(LB_ERR_NOMEM, "device allocation failed");
+    if (use_f64(c)) {
+        StepParams<double> p = make_params<double>(c, c->cur, c->cur, c->t);
+        lbk::launch_get_pops<double>(c->store, p, set, static_cast<double *>(tmp.p), c->stream);
+    } else {
+        StepParams<float> p = make_params<float>(c, c->cur, c->cur, c->t);
+        lbk::launch_get_pops<float>(c->store, p, set, static_cast<double *>(tmp.p), c->stream);
+    }
+    if (int e = launch_check(c, "get populations")) return e;
+    if (int e = cuda_check(c, cudaMemcpyAsync(dst, tmp.p, bytes, cudaMemcpyDeviceToHost, c->stream), "copy")) return e;
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "sync");
+}
+
+int lb_set_populations(lb_ctx *c, int32_t set, const double *src)
+{
+    if (int e = sticky(c)) return e;
+    if (!src || set < 0 || set > 1) return fail(LB_ERR_INVALID, "bad argument");
+    const size_t bytes = (size_t)c->q[set] * c->nx * c->ny * sizeof(double);
+    TmpBuf tmp(c, bytes);
+    if (!tmp.p) return fail(LB_ERR_NOMEM, "device allocation failed");
+    if (int e = cuda_check(c, cudaMemcpyAsync(tmp.p, src, bytes, cudaMemcpyHostToDevice, c->stream), "copy")) return e;
+    if (use_f64(c)) {
+        StepParams<double> p = make_params<double>(c, c->cur, c->cur, c->t);
+        lbk::launch_set_pops<double>(c->store, p, set, static_cast<const double *>(tmp.p), c->stream);
+    } else {
+        StepParams<float> p = make_params<float>(c, c->cur, c->cur, c->t);
+        lbk::launch_set_pops<float>(c->store, p, set, static_cast<const double *>(tmp.p), c->stream);
+    }
+    if (int e = launch_check(c, "set populations")) return e;
+    if (int e = finalize_level(c, c->cur)) return e;
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "sync");
+}
+
+int lb_state_bytes(lb_ctx *c, size_t *bytes)
+{
+    if (!c || !bytes) return fail(LB_ERR_INVALID, "null argument");
+    *bytes = c->set_bytes[0] + c->set_bytes[1];
+    return LB_OK;
+}
+
+int lb_state_load(lb_ctx *c, const void *src, size_t bytes)
+{
+    if (int e = sticky(c)) return e;
+    if (!src || bytes != c->set_bytes[0] + c->set_bytes[1]) return fail(LB_ERR_INVALID, "state size mismatch");
+    const char *s = static_cast<const char *>(src);
+    if (int e = cuda_check(c, cudaMemcpyAsync(c->planes[c->cur][0], s, c->set_bytes[0], cudaMemcpyHostToDevice, c->stream),
+                           "state load"))
+        return e;
+    if (int e = cuda_check(c, cudaMemcpyAsync(c->planes[c->cur][1], s + c->set_bytes[0], c->set_bytes[1],
+                                              cudaMemcpyHostToDevice, c->stream), "state load"))
+        return e;
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "state load sync");
+}
+
+int lb_state_store(lb_ctx *c, void *dst, size_t bytes)
+{
+    if (int e = sticky(c)) return e;
+    if (!dst || bytes != c->set_bytes[0] + c->set_bytes[1]) return fail(LB_ERR_INVALID, "state size mismatch");
+    char *d = static_cast<char *>(dst);
+    if (int e = cuda_check(c, cudaMemcpyAsync(d, c->planes[c->cur][0], c->set_bytes[0], cudaMemcpyDeviceToHost, c->stream),
+                           "state store"))
+        return e;
+    if (int e = cuda_check(c, cudaMemcpyAsync(d + c->set_bytes[0], c->planes[c->cur][1], c->set_bytes[1],
+                                              cudaMemcpyDeviceToHost, c->stream), "state store"))
+        return e;
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "state store sync");
+}
+
+struct lb_file_header {
+    char magic[8];
+    int32_t version, nx, ny, q0, q1, store, iface, pad;
+    int64_t step;
+    double t, dt, h, rho0;
+    uint64_t bytes;
+};
+
+int lb_save(lb_ctx *c, const char *path)
+{
+    if (int e = sticky(c)) return e;
+    if (!path) return fail(LB_ERR_INVALID, "null path");
+    size_t bytes = c->set_bytes[0] + c->set_bytes[1];
+    std::vector<char> buf(bytes);
+    if (int e = lb_state_store(c, buf.data(), bytes)) return e;
+    lb_file_header hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, "LBGBCKP", 8);
+    hd.version = 1;
+    hd.nx = c->nx; hd.ny = c->ny; hd.q0 = c->q[0]; hd.q1 = c->q[1]; hd.store = c->store; hd.iface = c->opts.iface;
+    hd.step = c->step; hd.t = c->t; hd.dt = c->dt; hd.h = c->h; hd.rho0 = c->opts.rho0; hd.bytes = bytes;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(LB_ERR_INVALID, std::string("cannot open ") + path);
+    bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 && std::fwrite(c->tmap.data(), 1, c->tmap.size(), f) == c->tmap.size() &&
+              std::fwrite(buf.data(), 1, bytes, f) == bytes;
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? LB_OK : fail(LB_ERR_INVALID, "write failed");
+}
+
+int lb_load(lb_ctx *c, const char *path)
+{
+    if (int e = sticky(c)) return e;
+    if (!path) return fail(LB_ERR_INVALID, "null path");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(LB_ERR_INVALID, std::string("cannot open ") + path);
+    lb_file_header hd;
+    size_t bytes = c->set_bytes[0] + c->set_bytes[1];
+    std::vector<uint8_t> tm(c->tmap.size());
+    std::vector<char> buf(bytes);
+    bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1;
+    ok = ok && std::memcmp(hd.magic, "LBGBCKP", 8) == 0 && hd.version == 1 && hd.nx == c->nx && hd.ny == c->ny &&
+         hd.q0 == c->q[0] && hd.q1 == c->q[1] && hd.store == c->store && hd.iface == c->opts.iface && hd.bytes == bytes &&
+         hd.dt == c->dt && hd.h == c->h && hd.rho0 == c->opts.rho0;
+    ok = ok && std::fread(tm.data(), 1, tm.size(), f) == tm.size() && std::fread(buf.data(), 1, bytes, f) == bytes;
+    std::fclose(f);
+    if (!ok) return fail(LB_ERR_INVALID, "checkpoint does not match this lattice");
+    c->tmap = tm;
+    c->iface_rows.clear();
+    for (int j = 0; j < c->ny; ++j)
+        if (c->tmap[(size_t)j * c->ntx] & LB_TILE_IFACE) c->iface_rows.push_back(j);
+    if (int e = upload_tiles(c)) return e;
+    if (int e = lb_state_load(c, buf.data(), bytes)) return e;
+    c->step = hd.step;
+    c->t = hd.t;
+    return LB_OK;
+}
+
+int lb_info(lb_ctx *c, double *dt, double *h, int64_t *step, double *time, int32_t *variant)
+{
+    if (!c) return fail(LB_ERR_INVALID, "null context");
+    if (variant) *variant = c->variant;
+    if (dt) *dt = c->dt;
+    if (h) *h = c->h;
+    if (step) *step = c->step;
+    if (time) *time = c->t;
+    return LB_OK;
+}
+
+int lb_sync(lb_ctx *c)
+{
+    if (!c) return fail(LB_ERR_INVALID, "null context");
+    if (c->status == LB_OK) cuda_check(c, cudaStreamSynchronize(c->stream), "sync");
+    check_reduction(c);
+    return c->status;
+}
+
+void lb_destroy(lb_ctx *c)
+{
+    if (!c) return;
+    free_all(c);
+    delete c;
+}
+
+}  // extern "C"

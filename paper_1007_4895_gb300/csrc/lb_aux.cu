@@ -1,0 +1,268 @@
+/*
+ * lb_aux.cu -- kernels around the step: initial equilibrium, population import /
+ * export in the canonical layout, moment fields, and the FP64 mass / residual
+ * reduction.
+ */
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "lb_common.cuh"
+
+namespace lbk {
+
+/* f = f_eq(rho, u) (Eq. (demoeq)) in every node's own set. One thread per node. */
+template <int ST>
+__global__ void init_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p, const double *rho,
+                            const double *ux, const double *uy)
+{
+    using T = typename Store<ST>::T;
+    using R = typename Store<ST>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (x >= p.nx) return;
+    const size_t n = (size_t)j * p.nx + x;
+    const int s = p.tmap[(size_t)j * p.ntx + x / LB_TILE_X] & LB_TILE_HIGH;
+    const SetConst<R> &c = p.set[s];
+    const R r = R(rho[n]), u = R(ux[n]), v = R(uy[n]);
+    const R rd = R(rho[n] - double(p.rho0)), usq = u * u + v * v;
+    const size_t plane = (size_t)p.ny * p.pitch;
+    T *f = static_cast<T *>(p.fout[s]);
+    for (int a = 0; a < c.q; ++a)
+        put1(p, f + a * plane + (size_t)j * p.pitch, x, encode<ST>(deq(rd, r, c.cx[a] * u + c.cy[a] * v, usq), c.w[a], p.rho0));
+}
+
+/* Canonical double [q][ny][nx] -> planes of set `set`, at nodes that use that set. */
+template <int ST>
+__global__ void set_pops_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p, int set,
+                                const double *src)
+{
+    using T = typename Store<ST>::T;
+    using R = typename Store<ST>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (x >= p.nx) return;
+    if ((p.tmap[(size_t)j * p.ntx + x / LB_TILE_X] & LB_TILE_HIGH) != set) return;
+    const SetConst<R> &c = p.set[set];
+    const size_t plane = (size_t)p.ny * p.pitch;
+    T *f = static_cast<T *>(p.fout[set]);
+    for (int a = 0; a < c.q; ++a) {
+        const double fv = src[((size_t)a * p.ny + j) * p.nx + x];
+        const R d = R(fv * double(c.winv[a]) - double(p.rho0));
+        put1(p, f + a * plane + (size_t)j * p.pitch, x, encode<ST>(d, c.w[a], p.rho0));
+    }
+}
+
+/* Planes of set `set` -> canonical double f [q][ny][nx] (every node). */
+template <int ST>
+__global__ void get_pops_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p, int set, double *dst)
+{
+    using T = typename Store<ST>::T;
+    using R = typename Store<ST>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (x >= p.nx) return;
+    const SetConst<R> &c = p.set[set];
+    const size_t plane = (size_t)p.ny * p.pitch;
+    const T *f = static_cast<const T *>(p.fin[set]) + (size_t)j * p.pitch + x + LB_GHOST;
+    for (int a = 0; a < c.q; ++a) {
+        const R d = decode<ST>(f[a * plane], c.winv[a], p.rho0);
+        dst[((size_t)a * p.ny + j) * p.nx + x] = double(c.w[a]) * (double(p.rho0) + double(d));
+    }
+}
+
+/* Moment fields of every node from its own set: rho, u, P_xy = sum f (xi-u)_x (xi-u)_y,
+ * Pi^neq = sum (f - f_eq) xi xi, q = (1/2) sum f |xi - u|^2 (xi - u). The rest-state
+ * part w rho0 is summed in closed form (Gaussian moments up to third order, exact for
+ * every set), so only deviations enter the sums. */
+template <int ST, typename OUT>
+__global__ void moments_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p, uint32_t mask,
+                               OUT *dst)
+{
+    using T = typename Store<ST>::T;
+    using R = typename Store<ST>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (x >= p.nx) return;
+    const int s = p.tmap[(size_t)j * p.ntx + x / LB_TILE_X] & LB_TILE_HIGH;
+    const SetConst<R> &c = p.set[s];
+    const size_t plane = (size_t)p.ny * p.pitch;
+    const T *f = static_cast<const T *>(p.fin[s]) + (size_t)j * p.pitch + x + LB_GHOST;
+    const R rho0 = p.rho0;
+    R d[LB_QMAX];
+    R rd = R(0), jx = R(0), jy = R(0);
+    for (int a = 0; a < c.q; ++a) {
+        d[a] = decode<ST>(f[a * plane], c.winv[a], rho0);
+        rd = fma(c.w[a], d[a], rd);
+        jx = fma(c.wcx[a], d[a], jx);
+        jy = fma(c.wcy[a], d[a], jy);
+    }
+    const R rho = rho0 + rd, ux = jx / rho, uy = jy / rho, usq = ux * ux + uy * uy;
+    /* rest-state parts: sum w (xi-u)_x (xi-u)_y = ux uy; sum w |xi-u|^2 (xi-u)_x = -ux (4 + u^2) */
+    R pxy = rho0 * ux * uy, nxx = R(0), nxy = R(0), nyy = R(0);
+    R qx = R(-0.5) * rho0 * ux * (R(4) + usq), qy = R(-0.5) * rho0 * uy * (R(4) + usq);
+    for (int a = 0; a < c.q; ++a) {
+        const R cx = c.cx[a], cy = c.cy[a];
+        const R wd = c.w[a] * d[a];
+        const R dx = cx - ux, dy = cy - uy, dd = dx * dx + dy * dy;
+        const R eu = cx * ux + cy * uy;
+        const R wne = c.w[a] * (d[a] - deq(rd, rho, eu, usq));
+        pxy = fma(wd, dx * dy, pxy);
+        nxx = fma(wne, cx * cx, nxx);
+        nxy = fma(wne, cx * cy, nxy);
+        nyy = fma(wne, cy * cy, nyy);
+        qx = fma(R(0.5) * wd, dd * dx, qx);
+        qy = fma(R(0.5) * wd, dd * dy, qy);
+    }
+    const R vals[9] = {rho, ux, uy, pxy, nxx, nxy, nyy, qx, qy};
+    const size_t N = (size_t)p.nx * p.ny, n = (size_t)j * p.nx + x;
+    int k = 0;
+    for (int m = 0; m < 9; ++m)
+        if (mask & (1u << m)) dst[(size_t)(k++) * N + n] = OUT(vals[m]);
+}
+
+/* FP64 sums over every node: mass, |u - u_prev|^2, |u|^2, count of non-finite nodes.
+ * Warp shuffles, then shared memory, then one partial per block; the last block to
+ * finish adds the partials in block order (deterministic) and resets the counter. */
+template <int ST>
+__global__ void reduce_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p,
+                              typename Store<ST>::R *uprev, double *part, unsigned int *counter, double *out)
+{
+    using T = typename Store<ST>::T;
+    using R = typename Store<ST>::R;
+    const size_t N = (size_t)p.nx * p.ny;
+    const size_t plane = (size_t)p.ny * p.pitch;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(n % p.nx), j = (int)(n / p.nx);
+        const int s = p.tmap[(size_t)j * p.ntx + x / LB_TILE_X] & LB_TILE_HIGH;
+        const SetConst<R> &c = p.set[s];
+        const T *f = static_cast<const T *>(p.fin[s]) + (size_t)j * p.pitch + x + LB_GHOST;
+        R rd = R(0), jx = R(0), jy = R(0);
+        for (int a = 0; a < c.q; ++a) {
+            const R d = decode<ST>(f[a * plane], c.winv[a], p.rho0);
+            rd = fma(c.w[a], d, rd);
+            jx = fma(c.wcx[a], d, jx);
+            jy = fma(c.wcy[a], d, jy);
+        }
+        const double rho = double(p.rho0) + double(rd);
+        const double ux = double(jx) / rho, uy = double(jy) / rho;
+        if (!isfinite(rho) || !isfinite(ux) || !isfinite(uy)) {
+            acc[3] += 1.0;
+            continue;
+        }
+        const double px = double(uprev[2 * n]), py = double(uprev[2 * n + 1]);
+        acc[0] += rho;
+        acc[1] += (ux - px) * (ux - px) + (uy - py) * (uy - py);
+        acc[2] += ux * ux + uy * uy;
+        uprev[2 * n] = R(ux);
+        uprev[2 * n + 1] = R(uy);
+    }
+    for (int m = 0; m < 4; ++m)
+        for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_down_sync(0xffffffffu, acc[m], o);
+    __shared__ double sh[32][4];
+    __shared__ bool last;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (lane == 0)
+        for (int m = 0; m < 4; ++m) sh[warp][m] = acc[m];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w)
+            for (int m = 0; m < 4; ++m) b[m] += sh[w][m];
+        for (int m = 0; m < 4; ++m) part[4 * blockIdx.x + m] = b[m];
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double t[4] = {0.0, 0.0, 0.0, 0.0};
+        for (unsigned b = 0; b < gridDim.x; ++b)
+            for (int m = 0; m < 4; ++m) t[m] += part[4 * b + m];
+        out[0] = t[0];
+        out[1] = t[2] > 0.0 ? sqrt(t[1] / t[2]) : 0.0;
+        out[2] = t[3];
+        *counter = 0u;
+    }
+}
+
+#define LB_DISPATCH(store, ...)                                   \
+    switch (store) {                                               \
+        case 0: { constexpr int ST = 0; __VA_ARGS__; } break;             \
+        case 1: { constexpr int ST = 1; __VA_ARGS__; } break;             \
+        case 2: { constexpr int ST = 2; __VA_ARGS__; } break;             \
+        case 3: { constexpr int ST = 3; __VA_ARGS__; } break;             \
+        default: { constexpr int ST = 4; __VA_ARGS__; } break;            \
+    }
+
+template <typename R, int ST>
+constexpr bool store_matches()
+{
+    return std::is_same<R, typename Store<ST>::R>::value;
+}
+
+template <typename R>
+void launch_init(int store, const StepParams<R> &p, const double *rho, const double *ux, const double *uy,
+                 void *stream)
+{
+    dim3 grid((p.nx + 127) / 128, p.ny);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) init_kernel<ST><<<grid, 128, 0, st>>>(p, rho, ux, uy));
+}
+
+template <typename R>
+void launch_set_pops(int store, const StepParams<R> &p, int set, const double *src, void *stream)
+{
+    dim3 grid((p.nx + 127) / 128, p.ny);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) set_pops_kernel<ST><<<grid, 128, 0, st>>>(p, set, src));
+}
+
+template <typename R>
+void launch_get_pops(int store, const StepParams<R> &p, int set, double *dst, void *stream)
+{
+    dim3 grid((p.nx + 127) / 128, p.ny);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) get_pops_kernel<ST><<<grid, 128, 0, st>>>(p, set, dst));
+}
+
+template <typename R>
+void launch_moments(int store, const StepParams<R> &p, uint32_t mask, void *dst, int dst_f64, void *stream)
+{
+    dim3 grid((p.nx + 127) / 128, p.ny);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (dst_f64) {
+        LB_DISPATCH(store, if constexpr (store_matches<R, ST>())
+                               moments_kernel<ST, double><<<grid, 128, 0, st>>>(p, mask, static_cast<double *>(dst)));
+    } else {
+        LB_DISPATCH(store, if constexpr (store_matches<R, ST>())
+                               moments_kernel<ST, float><<<grid, 128, 0, st>>>(p, mask, static_cast<float *>(dst)));
+    }
+}
+
+int reduce_blocks(int nx, int ny)
+{
+    long long n = (long long)nx * ny;
+    long long b = (n + 255) / 256;
+    if (b > 4 * 152) b = 4 * 152;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <typename R>
+void launch_reduce(int store, const StepParams<R> &p, R *uprev, double *part, unsigned int *counter, double *out,
+                   int nblocks, void *stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LB_DISPATCH(store, if constexpr (store_matches<R, ST>())
+                           reduce_kernel<ST><<<nblocks, 256, 0, st>>>(p, uprev, part, counter, out));
+}
+
+template void launch_init<float>(int, const StepParams<float> &, const double *, const double *, const double *, void *);
+template void launch_init<double>(int, const StepParams<double> &, const double *, const double *, const double *, void *);
+template void launch_set_pops<float>(int, const StepParams<float> &, int, const double *, void *);
+template void launch_set_pops<double>(int, const StepParams<double> &, int, const double *, void *);
+template void launch_get_pops<float>(int, const StepParams<float> &, int, double *, void *);
+template void launch_get_pops<double>(int, const StepParams<double> &, int, double *, void *);
+template void launch_moments<float>(int, const StepParams<float> &, uint32_t, void *, int, void *);
+template void launch_moments<double>(int, const StepParams<double> &, uint32_t, void *, int, void *);
+template void launch_reduce<float>(int, const StepParams<float> &, float *, double *, unsigned int *, double *, int, void *);
+template void launch_reduce<double>(int, const StepParams<double> &, double *, double *, unsigned int *, double *, int, void *);
+
+}  // namespace lbk

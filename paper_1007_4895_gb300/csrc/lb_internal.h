@@ -1,0 +1,104 @@
+/*
+ * lb_internal.h -- data layout and launch parameters shared by the host side of the
+ * library (lb_api.cu) and its kernels (lb_step.cu, lb_aux.cu).
+ *
+ * Device layout of one time level of one velocity set: Q planes, each [ny][pitch]
+ * elements, x contiguous. Logical column x lives at storage column x + LB_GHOST;
+ * the LB_GHOST columns on each side hold periodic images (periodic x) or copies of the
+ * boundary column (pressure sides), so the radius-2 stencil never wraps an index.
+ * Both sets have planes over the whole grid: a node's own set holds its state; the
+ * other set's planes hold, at nodes next to an interface, that node rebuilt in the
+ * other set (written by the step that produced the node), which is exactly what the
+ * readers of the other set need at the next step.
+ *
+ * The region map is kept per tile of LB_TILE_X columns x 1 row, one byte of flags.
+ */
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#define LB_GHOST 4
+#define LB_TILE_X 128
+#define LB_QMAX 36
+#define LB_MAX_IFACE 64
+
+enum : uint8_t {
+    LB_TILE_HIGH = 1u,     /* tile uses set 1 */
+    LB_TILE_SHADOW = 2u,   /* mode B: also write this tile rebuilt in the other set */
+    LB_TILE_IFACE = 4u,    /* mode A: interface row, set by the interface pass */
+    LB_TILE_NEAR_H = 8u,   /* mode A: interface row whose high-order neighbour is j - 1 */
+};
+
+template <typename R>
+struct SetConst {
+    int q;
+    int n1d;
+    R cx[LB_QMAX], cy[LB_QMAX];     /* abscissae xi_x, xi_y */
+    R w[LB_QMAX], winv[LB_QMAX];    /* weights and 1 / w */
+    R wcx[LB_QMAX], wcy[LB_QMAX];   /* w xi_x, w xi_y */
+    R crx[LB_QMAX], cry[LB_QMAX];   /* Courant numbers xi dt / h */
+    R kx[LB_QMAX], ky[LB_QMAX];     /* (1 - |Courant|) / 2 */
+    R wxx[LB_QMAX], wxy[LB_QMAX], wyy[LB_QMAX];   /* w (xi_x^2 - 1), w xi_x xi_y, w (xi_y^2 - 1) */
+    R hxx[LB_QMAX], hxy[LB_QMAX], hyy[LB_QMAX];   /* (xi_x^2 - 1) / 2, xi_x xi_y, (xi_y^2 - 1) / 2 */
+};
+
+template <typename R>
+struct StepParams {
+    int nx, ny, pitch, ntx;
+    const uint8_t *tmap;            /* [ny][ntx] tile flags */
+    const void *fin[2];             /* planes of the level read, per set */
+    void *fout[2];                  /* planes of the level written, per set */
+    R rho0, dt;
+    R kn_rho;                       /* kn_ref * rho_ref (tau = kn_rho / rho), or tau if const */
+    int tau_const;                  /* 1: tau = kn_rho */
+    R tau_shift;                    /* subtracted from tau (dt / 2 or 0) */
+    R gx, gy;
+    int has_force;
+    int periodic_x, periodic_y;
+    int wall_diffuse[2];            /* bottom, top */
+    int pressure[2];                /* left, right */
+    R rho_side[2];                  /* pressure densities, left / right */
+    R uw_x[2], uw_y[2];             /* wall velocities at the new time level */
+    R kin[2][2];                    /* [set][wall] sum_{in} |xi.n| w */
+    R kout[2][2];                   /* [set][wall] sum_{out} |xi.n| w S(u_W) / w */
+    R kdiff[2][2];                  /* kin - kout, formed in FP64 (zero for a tangential wall) */
+    int n_iface;                    /* mode A: interface rows (x-uniform bands) */
+    int iface_row[LB_MAX_IFACE];
+    SetConst<R> set[2];
+};
+
+/* storage codes match LB_STORE_* */
+namespace lbk {
+
+template <typename R>
+void launch_step(int store, const StepParams<R> &p, void *stream);
+/* variant 0 = one row per thread (lb_step.cu); 1..3 = register-window forms */
+template <typename R>
+void launch_step2(int store, int variant, const StepParams<R> &p, void *stream);
+#define LB_NUM_VARIANTS 4
+template <typename R>
+void launch_iface(int store, const StepParams<R> &p, void *stream);
+template <typename R>
+void launch_pressure(int store, const StepParams<R> &p, void *stream);
+template <typename R>
+void launch_shadows(int store, const StepParams<R> &p, void *stream);
+template <typename R>
+void launch_ghosts(int store, const StepParams<R> &p, void *stream);
+template <typename R>
+void launch_init(int store, const StepParams<R> &p, const double *rho, const double *ux, const double *uy,
+                 void *stream);
+template <typename R>
+void launch_set_pops(int store, const StepParams<R> &p, int set, const double *src, void *stream);
+template <typename R>
+void launch_get_pops(int store, const StepParams<R> &p, int set, double *dst, void *stream);
+template <typename R>
+void launch_moments(int store, const StepParams<R> &p, uint32_t mask, void *dst, int dst_f64, void *stream);
+/* partial sums per block into part[nblocks][4]; the last block folds them into out[4]
+ * in block order. uprev [ny][nx][2] (R) is read and replaced. */
+template <typename R>
+void launch_reduce(int store, const StepParams<R> &p, R *uprev, double *part, unsigned int *counter,
+                   double *out, int nblocks, void *stream);
+int reduce_blocks(int nx, int ny);
+
+}  // namespace lbk

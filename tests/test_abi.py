@@ -1,0 +1,86 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for sm_103a,
+loads, exports every entry point include/lb.h declares, and rejects bad arguments
+before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lb():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1007_4895_gb300 as lb
+    return lb
+
+
+def declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lb_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ("lb_create", "lb_step", "lb_moments", "lb_reductions", "lb_destroy", "lb_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lb):
+    so = ctypes.CDLL(lb.LIB_PATH)
+    missing = [n for n in sorted(declared_symbols()) if not hasattr(so, n)]
+    assert not missing, missing
+    assert set(lb.EXPORTS) == declared_symbols()
+
+
+def _args(lb, nx=8, ny=8, **over):
+    grid = lb.lb_grid(nx, ny, 0.0, 0.5, 0.0)
+    kn = lb.lb_kn(over.get("kn", 0.1), 1.0, 0)
+    walls = [lb.lb_wall(1, 0, 0, 1, 0), lb.lb_wall(1, 0, 0, 1, 0), lb.lb_wall(0, 0, 0, 1, 0), lb.lb_wall(0, 0, 0, 1, 0)]
+    for k, v in over.get("walls", {}).items():
+        walls[k] = v
+    opts = lb.lb_opts()
+    opts.store, opts.iface, opts.rho0 = over.get("store", 1), over.get("iface", 1), over.get("rho0", 1.0)
+    return grid, np.zeros((ny, nx), np.uint8), over.get("sets", (9, 36)), kn, walls, opts
+
+
+@pytest.mark.parametrize("case", [
+    dict(nx=2), dict(ny=3), dict(sets=(9, 25)), dict(store=9), dict(iface=5), dict(rho0=0.0), dict(kn=-1.0),
+    dict(kn=1e-6),                                  # dt / tau > 1
+    dict(walls={0: None}),                          # bottom periodic, top diffuse (filled below)
+])
+def test_invalid_arguments_are_rejected_on_the_host(lb, case):
+    over = dict(case)
+    if "walls" in over:
+        over["walls"] = {0: lb.lb_wall(0, 0, 0, 1, 0)}
+    nx, ny = over.pop("nx", 8), over.pop("ny", 8)
+    args = _args(lb, nx, ny, **over)
+    with pytest.raises(lb.LBError) as e:
+        lb.lb_create(*args)
+    assert e.value.code == lb.LB_ERR_INVALID
+    assert lb.lb_last_error()
+
+
+def test_region_map_values_checked(lb):
+    grid, m, sets, kn, walls, opts = _args(lb)
+    m[3, 3] = 2
+    with pytest.raises(lb.LBError) as e:
+        lb.lb_create(grid, m, sets, kn, walls, opts)
+    assert e.value.code == lb.LB_ERR_INVALID
+
+
+def test_paper_interface_mode_needs_x_uniform_rows(lb):
+    grid, m, sets, kn, walls, opts = _args(lb, nx=256, ny=16, iface=0)
+    m[:3, :128] = 1         # one 128-column tile high-order, its neighbour not
+    with pytest.raises(lb.LBError) as e:
+        lb.lb_create(grid, m, sets, kn, walls, opts)
+    assert e.value.code == lb.LB_ERR_INVALID
