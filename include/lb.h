@@ -123,8 +123,10 @@ typedef struct {
  * stream is a cudaStream_t. reduce_every > 0 runs the mass / residual reduction
  * every that many steps inside lb_step and flags divergence. variant < 0 lets
  * lb_create time the step-kernel layouts on this lattice and keep the fastest
- * (cached per process); 0 .. 3 forces one (0: one row per thread; 1, 2, 3: a
- * register window of 2, 3, 4 rows per thread). All layouts give the same result. */
+ * (cached per process); 0 or 1 forces one (0: one quad of nodes per thread, loads
+ * through L1; 1: tiles streamed through shared memory by the tensor memory
+ * accelerator, FP32 / FP16 / BF16 storage only, else 0 is used). All layouts give the
+ * same result. */
 typedef struct {
     int32_t store;
     int32_t iface;

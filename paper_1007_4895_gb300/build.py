@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lb_api.cu", "lb_step.cu", "lb_step2.cu", "lb_aux.cu", "quadrature.cpp"]
+SOURCES = ["lb_api.cu", "lb_step.cu", "lb_step_st_f64.cu", "lb_step_st_f32.cu", "lb_step_st_f32dev.cu",
+           "lb_step_st_f16.cu", "lb_step_st_bf16.cu", "lb_step3.cu", "lb_aux.cu", "quadrature.cpp"]
 
 
 def nvcc() -> str:
@@ -46,7 +47,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC,
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC", "-I", CSRC,
                      "--expt-relaxed-constexpr"]
     if verbose:
         common += ["-Xptxas", "-v"]

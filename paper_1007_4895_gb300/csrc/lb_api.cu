@@ -15,10 +15,12 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/lb.h"
 #include "lb_internal.h"
+#include "lb_tma.h"
 
 namespace lbq {
 int velocity_set(int q, double *cx, double *cy, double *w);
@@ -75,7 +77,10 @@ struct lb_ctx {
     double t = 0.0;
     int64_t step = 0;
     int status = LB_OK;
-    int variant = -1;               /* step kernel layout in use (see launch_step2) */
+    int variant = -1;               /* step kernel layout in use (see launch_variant) */
+    bool tma_ok = false;            /* tensor maps built (FP32 / FP16 / BF16 storage) */
+    TmaMaps maps[2];                /* per time level */
+    int *d_err = nullptr;           /* bounded device waits that ran out */
     std::vector<void *> owned;
 };
 
@@ -157,10 +162,12 @@ StepParams<R> make_params(const lb_ctx *c, int in, int out, double t_new)
     p.pitch = c->pitch;
     p.ntx = c->ntx;
     p.tmap = c->d_tmap;
+    const size_t row0 = (size_t)LB_GHOST_ROWS * c->pitch * c->esize;   /* logical row 0 */
     for (int s = 0; s < 2; ++s) {
-        p.fin[s] = c->planes[in][s];
-        p.fout[s] = c->planes[out][s];
+        p.fin[s] = static_cast<const char *>(c->planes[in][s]) + row0;
+        p.fout[s] = static_cast<char *>(c->planes[out][s]) + row0;
     }
+    p.plane = (size_t)(c->ny + 2 * LB_GHOST_ROWS) * c->pitch;
     p.rho0 = R(c->opts.rho0);
     p.dt = R(c->dt);
     p.tau_const = c->kn.rho_ref > 0.0 ? 0 : 1;
@@ -299,11 +306,16 @@ int upload_tiles(lb_ctx *c)
                       "tile map upload");
 }
 
+/* variant 0: one node quad per thread (lb_step_impl.cuh); 1: TMA-fed producer /
+ * consumer blocks (lb_step3.cu, not for FP64 storage). */
 template <typename R>
 void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
 {
-    if (variant <= 0) lbk::launch_step<R>(c->store, p, c->stream);
-    else lbk::launch_step2<R>(c->store, variant, p, c->stream);
+    if constexpr (std::is_same<R, float>::value) {
+        if (variant == 1 && c->tma_ok && lbk::launch_step3(c->store, p, c->maps[c->cur], c->d_err, c->stream) == 0)
+            return;
+    }
+    lbk::launch_step<R>(c->store, p, c->stream);
 }
 
 /* Autotuner: times every step-kernel layout on this lattice (reading the current level,
@@ -324,7 +336,7 @@ int autotune_t(lb_ctx *c)
         auto it = g_tune.find(key);
         if (it != g_tune.end()) return it->second;
     }
-    const int nvar = use_f64(c) ? 2 : LB_NUM_VARIANTS;
+    const int nvar = c->tma_ok ? LB_NUM_VARIANTS : 1;
     StepParams<R> p = make_params<R>(c, c->cur, c->cur ^ 1, c->t + c->dt);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -354,7 +366,7 @@ int autotune_t(lb_ctx *c)
 
 int choose_variant(lb_ctx *c)
 {
-    if (c->opts.variant >= 0) return c->opts.variant < LB_NUM_VARIANTS ? c->opts.variant : 1;
+    if (c->opts.variant >= 0) return (c->opts.variant == 1 && !c->tma_ok) ? 0 : c->opts.variant;
     return use_f64(c) ? autotune_t<double>(c) : autotune_t<float>(c);
 }
 
@@ -424,6 +436,75 @@ void *own(lb_ctx *c, size_t bytes)
     void *p = dev_alloc(c, bytes);
     if (p) c->owned.push_back(p);
     return p;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+/* Tensor maps over (storage column, storage row, plane) of every level and set. */
+bool make_maps(lb_ctx *c)
+{
+    if (c->store == LB_STORE_F64) return false;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const CUtensorMapDataType dt = c->store == LB_STORE_F16_DEV    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : c->store == LB_STORE_BF16_DEV ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t rows = (cuuint64_t)c->ny + 2 * LB_GHOST_ROWS;
+    for (int lv = 0; lv < 2; ++lv)
+        for (int s = 0; s < 2; ++s) {
+            const cuuint64_t dims[3] = {(cuuint64_t)c->pitch, rows, (cuuint64_t)c->q[s]};
+            const cuuint64_t strides[2] = {(cuuint64_t)c->pitch * c->esize, (cuuint64_t)c->pitch * rows * c->esize};
+            const cuuint32_t estr[3] = {1, 1, 1};
+            const cuuint32_t np = (cuuint32_t)lbk::step3_planes();
+            const cuuint32_t b1[3] = {(cuuint32_t)lbk::step3_cols(), (cuuint32_t)lbk::step3_rows(), np};
+            const cuuint32_t b2[3] = {(cuuint32_t)lbk::step3_cols(), (cuuint32_t)lbk::step3_rows() + 4, np};
+            if (enc(&c->maps[lv].box1[s], dt, 3, c->planes[lv][s], dims, strides, b1, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return false;
+            if (enc(&c->maps[lv].box2[s], dt, 3, c->planes[lv][s], dims, strides, b2, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return false;
+        }
+    return true;
+}
+
+/* A bounded wait inside a kernel ran out: the context is left in LB_ERR_TIMEOUT. */
+int check_device_error(lb_ctx *c)
+{
+    if (!c->d_err || c->status != LB_OK) return c->status;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        c->status = LB_ERR_CUDA;
+        g_err = "reading the device error word failed";
+        return c->status;
+    }
+    if (h != 0) {
+        c->status = LB_ERR_TIMEOUT;
+        g_err = "a bounded device wait ran out in the step kernel";
+    }
+    return c->status;
 }
 
 struct TmpBuf {
@@ -514,7 +595,8 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
         delete c;
         return e;
     }
-    for (int s = 0; s < 2; ++s) c->set_bytes[s] = (size_t)c->q[s] * c->ny * c->pitch * c->esize;
+    for (int s = 0; s < 2; ++s)
+        c->set_bytes[s] = (size_t)c->q[s] * (c->ny + 2 * LB_GHOST_ROWS) * c->pitch * c->esize;
     for (int lv = 0; lv < 2; ++lv)
         for (int s = 0; s < 2; ++s) c->planes[lv][s] = own(c, c->set_bytes[s]);
     c->d_tmap = static_cast<uint8_t *>(own(c, c->tmap.size()));
@@ -523,7 +605,8 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
     c->d_out = static_cast<double *>(own(c, sizeof(double) * 4));
     c->d_counter = static_cast<unsigned int *>(own(c, 256));
     c->d_uprev = own(c, (size_t)c->nx * c->ny * 2 * (use_f64(c) ? 8 : 4));
-    bool ok = c->d_tmap && c->d_part && c->d_out && c->d_counter && c->d_uprev;
+    c->d_err = static_cast<int *>(own(c, 256));
+    bool ok = c->d_tmap && c->d_part && c->d_out && c->d_counter && c->d_uprev && c->d_err;
     for (int lv = 0; lv < 2; ++lv)
         for (int s = 0; s < 2; ++s) ok = ok && c->planes[lv][s];
     if (!ok) {
@@ -543,12 +626,14 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
     for (int lv = 0; lv < 2 && ce == cudaSuccess; ++lv)
         for (int s = 0; s < 2 && ce == cudaSuccess; ++s) ce = cudaMemsetAsync(c->planes[lv][s], 0, c->set_bytes[s], c->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->d_counter, 0, 256, c->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(c->d_err, 0, 256, c->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->d_uprev, 0, (size_t)c->nx * c->ny * 2 * (use_f64(c) ? 8 : 4), c->stream);
     if (ce != cudaSuccess || upload_tiles(c) != LB_OK) {
         free_all(c);
         delete c;
         return fail(LB_ERR_CUDA, std::string("initial fill failed: ") + cudaGetErrorString(ce));
     }
+    c->tma_ok = make_maps(c);
     *out = c;
     e = lb_init_equilibrium(c, nullptr, nullptr, nullptr);
     if (e) {
@@ -651,6 +736,7 @@ int lb_reductions(lb_ctx *c, double out[4])
                            "reduce copy"))
         return e;
     if (int e = cuda_check(c, cudaStreamSynchronize(c->stream), "reduce sync")) return e;
+    if (int e = check_device_error(c)) return fail(e, g_err);
     c->red_pending = false;
     out[0] = c->h_out[0];
     out[1] = c->h_out[1];
@@ -849,6 +935,7 @@ int lb_sync(lb_ctx *c)
     if (!c) return fail(LB_ERR_INVALID, "null context");
     if (c->status == LB_OK) cuda_check(c, cudaStreamSynchronize(c->stream), "sync");
     check_reduction(c);
+    check_device_error(c);
     return c->status;
 }
 

@@ -25,10 +25,10 @@ __global__ void init_kernel(const __grid_constant__ StepParams<typename Store<ST
     const SetConst<R> &c = p.set[s];
     const R r = R(rho[n]), u = R(ux[n]), v = R(uy[n]);
     const R rd = R(rho[n] - double(p.rho0)), usq = u * u + v * v;
-    const size_t plane = (size_t)p.ny * p.pitch;
+    const size_t plane = p.plane;
     T *f = static_cast<T *>(p.fout[s]);
     for (int a = 0; a < c.q; ++a)
-        put1(p, f + a * plane + (size_t)j * p.pitch, x, encode<ST>(deq(rd, r, c.cx[a] * u + c.cy[a] * v, usq), c.w[a], p.rho0));
+        put1r(p, f + a * plane + (size_t)j * p.pitch, x, j, encode<ST>(deq(rd, r, c.cx[a] * u + c.cy[a] * v, usq), c.w[a], p.rho0));
 }
 
 /* Canonical double [q][ny][nx] -> planes of set `set`, at nodes that use that set. */
@@ -42,12 +42,12 @@ __global__ void set_pops_kernel(const __grid_constant__ StepParams<typename Stor
     if (x >= p.nx) return;
     if ((p.tmap[(size_t)j * p.ntx + x / LB_TILE_X] & LB_TILE_HIGH) != set) return;
     const SetConst<R> &c = p.set[set];
-    const size_t plane = (size_t)p.ny * p.pitch;
+    const size_t plane = p.plane;
     T *f = static_cast<T *>(p.fout[set]);
     for (int a = 0; a < c.q; ++a) {
         const double fv = src[((size_t)a * p.ny + j) * p.nx + x];
         const R d = R(fv * double(c.winv[a]) - double(p.rho0));
-        put1(p, f + a * plane + (size_t)j * p.pitch, x, encode<ST>(d, c.w[a], p.rho0));
+        put1r(p, f + a * plane + (size_t)j * p.pitch, x, j, encode<ST>(d, c.w[a], p.rho0));
     }
 }
 
@@ -60,7 +60,7 @@ __global__ void get_pops_kernel(const __grid_constant__ StepParams<typename Stor
     const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (x >= p.nx) return;
     const SetConst<R> &c = p.set[set];
-    const size_t plane = (size_t)p.ny * p.pitch;
+    const size_t plane = p.plane;
     const T *f = static_cast<const T *>(p.fin[set]) + (size_t)j * p.pitch + x + LB_GHOST;
     for (int a = 0; a < c.q; ++a) {
         const R d = decode<ST>(f[a * plane], c.winv[a], p.rho0);
@@ -82,7 +82,7 @@ __global__ void moments_kernel(const __grid_constant__ StepParams<typename Store
     if (x >= p.nx) return;
     const int s = p.tmap[(size_t)j * p.ntx + x / LB_TILE_X] & LB_TILE_HIGH;
     const SetConst<R> &c = p.set[s];
-    const size_t plane = (size_t)p.ny * p.pitch;
+    const size_t plane = p.plane;
     const T *f = static_cast<const T *>(p.fin[s]) + (size_t)j * p.pitch + x + LB_GHOST;
     const R rho0 = p.rho0;
     R d[LB_QMAX];
@@ -127,7 +127,7 @@ __global__ void reduce_kernel(const __grid_constant__ StepParams<typename Store<
     using T = typename Store<ST>::T;
     using R = typename Store<ST>::R;
     const size_t N = (size_t)p.nx * p.ny;
-    const size_t plane = (size_t)p.ny * p.pitch;
+    const size_t plane = p.plane;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
         const int x = (int)(n % p.nx), j = (int)(n / p.nx);

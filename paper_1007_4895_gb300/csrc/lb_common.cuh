@@ -10,6 +10,32 @@
 
 namespace lbk {
 
+/* Per-population constants as read inside the population loops: two 16-byte records
+ * (FP32) per population, staged in shared memory once per block, because indexing the
+ * kernel-parameter tables with a run-time population index goes through the L1 path on
+ * every access. */
+template <typename R>
+struct alignas(4 * sizeof(R)) PopC {
+    R cx, cy, crx, cry;   /* xi and Courant numbers */
+    R kx, ky, w, winv;    /* limiter factors (1 - |c|) / 2, weight, 1 / weight */
+};
+template <typename R>
+struct alignas(4 * sizeof(R)) MomC {
+    R w, wcx, wcy, winv;
+};
+
+template <typename R>
+__device__ __forceinline__ void stage_consts(const StepParams<R> &p, PopC<R> (*pc)[LB_QMAX], MomC<R> (*mc)[LB_QMAX],
+                                             int tid, int nthreads)
+{
+    for (int k = tid; k < 2 * LB_QMAX; k += nthreads) {
+        const int s = k / LB_QMAX, a = k % LB_QMAX;
+        const SetConst<R> &c = p.set[s];
+        pc[s][a] = PopC<R>{c.cx[a], c.cy[a], c.crx[a], c.cry[a], c.kx[a], c.ky[a], c.w[a], c.winv[a]};
+        mc[s][a] = MomC<R>{c.w[a], c.wcx[a], c.wcy[a], c.winv[a]};
+    }
+}
+
 /* Row j + offset with ghost = wall node (Sec. 3.2) or a periodic image. |offset| <= 2. */
 template <typename R>
 __device__ __forceinline__ int row_at(const StepParams<R> &p, int j)
@@ -51,6 +77,32 @@ __device__ __forceinline__ void put1(const StepParams<R> &p, T *prow, int x, T e
         if (x < LB_GHOST) prow[x + p.nx + LB_GHOST] = e;
         if (x >= p.nx - LB_GHOST) prow[x - p.nx + LB_GHOST] = e;
     }
+}
+
+/* Ghost rows that hold a copy of row j: the two rows beyond a wall row (ghost node =
+ * wall node) or, for periodic y, the images of rows 0, 1, ny-2, ny-1. Returns the
+ * number written to img (0..2) as row offsets relative to j. */
+template <typename R>
+__device__ __forceinline__ int row_images(const StepParams<R> &p, int j, int img[2])
+{
+    if (p.periodic_y) {
+        if (j == 0 || j == 1) { img[0] = p.ny; return 1; }
+        if (j == p.ny - 1 || j == p.ny - 2) { img[0] = -p.ny; return 1; }
+        return 0;
+    }
+    if (j == 0) { img[0] = -1; img[1] = -2; return 2; }
+    if (j == p.ny - 1) { img[0] = 1; img[1] = 2; return 2; }
+    return 0;
+}
+
+/* put1 on row j and on its ghost-row copies. */
+template <typename T, typename R>
+__device__ __forceinline__ void put1r(const StepParams<R> &p, T *prow, int x, int j, T e)
+{
+    put1(p, prow, x, e);
+    int img[2];
+    const int n = row_images(p, j, img);
+    for (int k = 0; k < n; ++k) put1(p, prow + (ptrdiff_t)img[k] * p.pitch, x, e);
 }
 
 /* Second-order Hermite coefficients of a node from its deviations in its own set:

@@ -2,10 +2,14 @@
  * lb_internal.h -- data layout and launch parameters shared by the host side of the
  * library (lb_api.cu) and its kernels (lb_step.cu, lb_aux.cu).
  *
- * Device layout of one time level of one velocity set: Q planes, each [ny][pitch]
- * elements, x contiguous. Logical column x lives at storage column x + LB_GHOST;
- * the LB_GHOST columns on each side hold periodic images (periodic x) or copies of the
- * boundary column (pressure sides), so the radius-2 stencil never wraps an index.
+ * Device layout of one time level of one velocity set: Q planes, each
+ * [ny + 2 LB_GHOST_ROWS][pitch] elements, x contiguous. Logical column x lives at
+ * storage column x + LB_GHOST, logical row j at storage row j + LB_GHOST_ROWS. The ghost
+ * columns hold periodic images (periodic x) or copies of the boundary column (pressure
+ * sides); the ghost rows hold copies of the wall row (Sec. 3.2: ghost node = wall node)
+ * or periodic images. So the radius-2 stencil never wraps or clamps an index, and a
+ * tile plus its halo is one dense box (what the TMA loads). Pointers handed to kernels
+ * point at logical row 0, column 0 - LB_GHOST.
  * Both sets have planes over the whole grid: a node's own set holds its state; the
  * other set's planes hold, at nodes next to an interface, that node rebuilt in the
  * other set (written by the step that produced the node), which is exactly what the
@@ -19,6 +23,7 @@
 #include <cstdint>
 
 #define LB_GHOST 4
+#define LB_GHOST_ROWS 2
 #define LB_TILE_X 128
 #define LB_QMAX 36
 #define LB_MAX_IFACE 64
@@ -46,6 +51,7 @@ struct SetConst {
 template <typename R>
 struct StepParams {
     int nx, ny, pitch, ntx;
+    size_t plane;                   /* elements per plane, (ny + 2 LB_GHOST_ROWS) * pitch */
     const uint8_t *tmap;            /* [ny][ntx] tile flags */
     const void *fin[2];             /* planes of the level read, per set */
     void *fout[2];                  /* planes of the level written, per set */
@@ -71,20 +77,17 @@ struct StepParams {
 /* storage codes match LB_STORE_* */
 namespace lbk {
 
+/* step kernel layouts: 0 = one node quad per thread (lb_step_impl.cuh),
+ * 1 = TMA-fed producer / consumer blocks (lb_step3.cu, FP32 / FP16 / BF16 storage) */
 template <typename R>
 void launch_step(int store, const StepParams<R> &p, void *stream);
-/* variant 0 = one row per thread (lb_step.cu); 1..3 = register-window forms */
-template <typename R>
-void launch_step2(int store, int variant, const StepParams<R> &p, void *stream);
-#define LB_NUM_VARIANTS 4
+#define LB_NUM_VARIANTS 2
 template <typename R>
 void launch_iface(int store, const StepParams<R> &p, void *stream);
 template <typename R>
 void launch_pressure(int store, const StepParams<R> &p, void *stream);
 template <typename R>
 void launch_shadows(int store, const StepParams<R> &p, void *stream);
-template <typename R>
-void launch_ghosts(int store, const StepParams<R> &p, void *stream);
 template <typename R>
 void launch_init(int store, const StepParams<R> &p, const double *rho, const double *ux, const double *uy,
                  void *stream);

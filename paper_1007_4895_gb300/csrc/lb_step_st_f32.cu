@@ -1,0 +1,7 @@
+/* Step kernel instantiated for one storage format (kept in its own translation unit
+ * so the formats compile in parallel). */
+#include "lb_step_impl.cuh"
+
+namespace lbk {
+template void launch_step_store<1>(const StepParams<typename Store<1>::R> &, void *);
+}

@@ -188,4 +188,21 @@ __device__ __forceinline__ void st4<__nv_bfloat16>(__nv_bfloat16 *p, const __nv_
 __device__ __forceinline__ float minmod(float a, float b) { return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.0f)); }
 __device__ __forceinline__ double minmod(double a, double b) { return fmax(fmin(a, b), fmin(fmax(a, b), 0.0)); }
 
+/* The same median written as max(min(a, b), min(a, 0), min(b, 0)), with the
+ * negative parts an = min(a, 0), bn = min(b, 0) supplied by the caller: along a row of
+ * differences each one serves two neighbouring faces, so its negative part is formed
+ * once. FP32 uses the three-input max of sm_100+. */
+__device__ __forceinline__ float neg_part(float a) { return fminf(a, 0.0f); }
+__device__ __forceinline__ double neg_part(double a) { return fmin(a, 0.0); }
+__device__ __forceinline__ float minmod_n(float a, float b, float an, float bn)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(fminf(a, b)), "f"(an), "f"(bn));
+    return r;
+}
+__device__ __forceinline__ double minmod_n(double a, double b, double an, double bn)
+{
+    return fmax(fmin(a, b), fmax(an, bn));
+}
+
 }  // namespace lbk

@@ -1,0 +1,23 @@
+/*
+ * lb_tma.h -- tensor maps for the TMA-fed step kernel (lb_step3.cu).
+ *
+ * One map per set and box shape over the 3-D storage of a time level:
+ * (storage column, storage row, population plane) with extents (pitch, ny + 4, Q).
+ */
+#pragma once
+
+#include <cuda.h>
+
+#include "lb_internal.h"
+
+struct TmaMaps {
+    CUtensorMap box1[2];   /* per set: 136 columns x LB3_R rows x LB3_NP planes (a unit's rows) */
+    CUtensorMap box2[2];   /* per set: 136 columns x (LB3_R + 4) rows x LB3_NP planes (plus the y halo) */
+};
+
+namespace lbk {
+int launch_step3(int store, const StepParams<float> &p, const TmaMaps &maps, int *err, void *stream);
+int step3_rows();
+int step3_cols();
+int step3_planes();
+}  // namespace lbk
