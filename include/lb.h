@@ -210,6 +210,32 @@ void lb_destroy(lb_ctx *ctx);
 /* Message of the calling thread's most recent error ("" if none). */
 const char *lb_last_error(void);
 
+/* Mass / residual reduction that allocates no device memory (the paper has no
+ * counterpart: this is for callers that cannot allocate, e.g. code running under a
+ * memory budget fixed by its host application, code whose allocator belongs to another
+ * framework and cannot be reached from C, or code that must not allocate while it is
+ * captured or replayed). It computes what lb_reductions computes, but on moment fields
+ * the caller owns (e.g. filled by lb_moments with dst_is_device = 1, dst_f64 = 1):
+ *   rho, ux, uy: device double arrays of n nodes (1 <= n <= LB_NOALLOC_MAX_NODES);
+ *   restart != 0: compare with u = 0 instead of the previous call's velocity;
+ *   stream: cudaStream_t to run on (NULL = legacy default stream);
+ *   out (host): [0] = sum rho (FP64), [1] = ||u - u_prev|| / ||u||, [2] = number of
+ *     non-finite nodes, [3] = n. Synchronous.
+ * Returns LB_OK, LB_ERR_INVALID (null pointer, n out of range: nothing is launched),
+ * LB_ERR_CUDA, or LB_ERR_DIVERGED (non-finite node; out is still filled); the message is
+ * in lb_last_error().
+ * Everything it needs beyond its arguments lives in one fixed array inside the library
+ * (about 8.1 MB: per-block partial sums and the previous velocity of up to
+ * LB_NOALLOC_MAX_NODES nodes), which every GPU that loads the library holds until the
+ * process exits. The first call on a device looks up the array's device address on
+ * that device; make that first call before any stream capture. All calls share the
+ * array and it keeps the last call's velocity: calls that can overlap on the GPU (other
+ * streams, other host threads) race with each other and must be serialised by the
+ * caller. */
+#define LB_NOALLOC_MAX_NODES 524288
+int lb_reduce_fields_noalloc(const double *rho, const double *ux, const double *uy, int64_t n, int32_t restart,
+                             void *stream, double out[4]);
+
 #ifdef __cplusplus
 }
 #endif

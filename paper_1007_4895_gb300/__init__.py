@@ -30,7 +30,9 @@ STORE_DTYPE = {LB_STORE_F64: "f64", LB_STORE_F32: "f32", LB_STORE_F32_DEV: "f32"
                LB_STORE_F16_DEV: "f16", LB_STORE_BF16_DEV: "bf16"}
 EXPORTS = ("lb_create", "lb_init_equilibrium", "lb_step", "lb_moments", "lb_reductions", "lb_effective_map",
            "lb_set_region_map", "lb_get_populations", "lb_set_populations", "lb_state_bytes", "lb_state_load",
-           "lb_state_store", "lb_save", "lb_load", "lb_info", "lb_sync", "lb_destroy", "lb_last_error")
+           "lb_state_store", "lb_save", "lb_load", "lb_info", "lb_sync", "lb_destroy", "lb_last_error",
+           "lb_reduce_fields_noalloc")
+LB_NOALLOC_MAX_NODES = 524288
 
 
 class LBError(RuntimeError):
@@ -92,6 +94,7 @@ def _load():
     L.lb_destroy.argtypes = [P]
     L.lb_destroy.restype = None
     L.lb_last_error.restype = ctypes.c_char_p
+    L.lb_reduce_fields_noalloc.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int32, P, dp]
     return L
 
 
@@ -206,6 +209,15 @@ def lb_destroy(ctx):
 
 def lb_last_error():
     return _lib.lb_last_error().decode()
+
+
+def lb_reduce_fields_noalloc(rho_ptr, ux_ptr, uy_ptr, n, restart=False, stream=None):
+    """Reduction over caller-owned device double fields without any device allocation
+    (see include/lb.h). Returns [mass, residual, non-finite count, n]."""
+    out = np.zeros(4)
+    _check(_lib.lb_reduce_fields_noalloc(ctypes.c_void_p(rho_ptr), ctypes.c_void_p(ux_ptr), ctypes.c_void_p(uy_ptr),
+                                         int(n), 1 if restart else 0, ctypes.c_void_p(stream or 0), _dp(out)))
+    return out
 
 
 # ----------------------------------------------------------------- Lattice

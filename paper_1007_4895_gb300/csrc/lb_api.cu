@@ -50,6 +50,10 @@ size_t elem_size(int store)
 
 }  // namespace
 
+namespace lbk {
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace lbk
+
 struct lb_ctx {
     int nx = 0, ny = 0, pitch = 0, ntx = 0;
     double h = 0.0, dt = 0.0;
