@@ -210,6 +210,62 @@ void lb_destroy(lb_ctx *ctx);
 /* Message of the calling thread's most recent error ("" if none). */
 const char *lb_last_error(void);
 
+/* ---------------------------------------------------------------------------------
+ * Learned interface placement. Sec. 2.2 leaves the switching criterion open (it cites
+ * local Knudsen numbers and stress / heat-flux based breakdown parameters). This part
+ * lets a small network choose, between steps, which tiles use the high-order set:
+ * 8 features per node -> 64 -> 64 -> 1 with GELU (erf form) hidden layers and a sigmoid
+ * output p(high-order set needed); trained in FP32, run with BF16 weights and FP32
+ * accumulation. Parameters: 4801 floats laid out W1 [64][8], b1 [64], W2 [64][64],
+ * b2 [64], W3 [64], b3 [1]; inputs are normalised as (x - mean) / scale.
+ * ------------------------------------------------------------------------------- */
+
+/* Features of every node of the current level into device float dst [8][ny][nx]:
+ * Pi^neq_xx / rho, Pi^neq_xy / rho, Pi^neq_yy / rho, q_x / rho, q_y / rho, distance to
+ * the nearest diffuse wall (in l0), local Kn (kn_ref rho_ref / rho, Eq. (KN)) and
+ * Kn |grad rho| / rho (central differences). Asynchronous. */
+int lb_features(lb_ctx *ctx, float *dst);
+
+/* Training label source, device float dst [ny][nx]: the part of each node's
+ * populations that a second-order Hermite expansion (Eq. (approxf), N = 2) cannot hold,
+ * per unit mass: ||f - P2 f|| / rho in the norm ||g||^2 = sum_a g_a^2 / w_a, from the
+ * node's own set (0 at equilibrium and for any second-order disturbance). Asynchronous. */
+int lb_hermite_residual(lb_ctx *ctx, float *dst);
+
+typedef struct lb_mlp lb_mlp;
+
+/* params: host float [4801]; norm: host float {mean[8], scale[8]} (scale > 0); device
+ * memory and stream come from opts (alloc / free / alloc_user / stream; other fields
+ * are ignored). */
+int lb_mlp_create(const float *params, const float norm[16], const lb_opts *opts, lb_mlp **out);
+/* Mean binary cross-entropy gradient over n samples (x: device float [8][n] raw
+ * features, column k = sample k; y: device float [n] in {0, 1}) into host grad [4801];
+ * the loss into *loss. n <= 2^20. Synchronous. */
+int lb_mlp_grad(lb_mlp *m, const float *x, const float *y, int64_t n, float *grad, double *loss);
+/* One full-batch Adam step (beta 0.9 / 0.999, eps 1e-8) with learning rate lr. */
+int lb_mlp_adam_step(lb_mlp *m, const float *x, const float *y, int64_t n, float lr);
+/* Mini-batch Adam training: epochs passes over the n samples in an order shuffled from
+ * seed, batches of `batch`; *last_epoch_loss = mean loss over the last epoch. */
+int lb_mlp_train(lb_mlp *m, const float *x, const float *y, int64_t n, int32_t epochs, int32_t batch, float lr,
+                 uint64_t seed, double *last_epoch_loss);
+int lb_mlp_get_params(lb_mlp *m, float *params);
+/* p [n] (device) from x [8][n] (device) with the BF16 copy of the weights. Synchronous. */
+int lb_mlp_infer(lb_mlp *m, const float *x, int64_t n, float *p);
+void lb_mlp_destroy(lb_mlp *m);
+
+/* Attach a network to a lattice (NULL detaches: the map stays as it is). Every `every`
+ * steps lb_step evaluates p at every node, takes its maximum per tile, turns a tile
+ * high-order when it reaches p_on and back to low-order when it drops below p_off
+ * (0 <= p_off < p_on <= 1), keeps the two rows next to each diffuse wall high-order,
+ * and rebuilds moved tiles in their new set (as lb_set_region_map). A non-finite p
+ * keeps the current map (counted as a fallback). Needs LB_IFACE_HERMITE. The network
+ * must outlive its use by the lattice. */
+int lb_set_mlp(lb_ctx *ctx, lb_mlp *m, int32_t every, float p_on, float p_off);
+/* Run that update now (synchronous). */
+int lb_learned_map_now(lb_ctx *ctx);
+/* Map updates run, fallbacks taken, and the share of nodes on high-order tiles. */
+int lb_map_stats(lb_ctx *ctx, int64_t *updates, int64_t *fallbacks, double *high_fraction);
+
 /* Mass / residual reduction that allocates no device memory (the paper has no
  * counterpart: this is for callers that cannot allocate, e.g. code running under a
  * memory budget fixed by its host application, code whose allocator belongs to another

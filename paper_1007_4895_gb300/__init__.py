@@ -31,7 +31,9 @@ STORE_DTYPE = {LB_STORE_F64: "f64", LB_STORE_F32: "f32", LB_STORE_F32_DEV: "f32"
 EXPORTS = ("lb_create", "lb_init_equilibrium", "lb_step", "lb_moments", "lb_reductions", "lb_effective_map",
            "lb_set_region_map", "lb_get_populations", "lb_set_populations", "lb_state_bytes", "lb_state_load",
            "lb_state_store", "lb_save", "lb_load", "lb_info", "lb_sync", "lb_destroy", "lb_last_error",
-           "lb_reduce_fields_noalloc")
+           "lb_reduce_fields_noalloc", "lb_features", "lb_hermite_residual", "lb_mlp_create", "lb_mlp_grad",
+           "lb_mlp_adam_step", "lb_mlp_train", "lb_mlp_get_params", "lb_mlp_infer", "lb_mlp_destroy", "lb_set_mlp",
+           "lb_learned_map_now", "lb_map_stats")
 LB_NOALLOC_MAX_NODES = 524288
 
 
@@ -95,6 +97,21 @@ def _load():
     L.lb_destroy.restype = None
     L.lb_last_error.restype = ctypes.c_char_p
     L.lb_reduce_fields_noalloc.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int32, P, dp]
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.lb_features.argtypes = [P, P]
+    L.lb_hermite_residual.argtypes = [P, P]
+    L.lb_mlp_create.argtypes = [fp, fp, ctypes.POINTER(lb_opts), ctypes.POINTER(P)]
+    L.lb_mlp_grad.argtypes = [P, P, P, ctypes.c_int64, fp, dp]
+    L.lb_mlp_adam_step.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_float]
+    L.lb_mlp_train.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                               ctypes.c_uint64, dp]
+    L.lb_mlp_get_params.argtypes = [P, fp]
+    L.lb_mlp_infer.argtypes = [P, P, ctypes.c_int64, P]
+    L.lb_mlp_destroy.argtypes = [P]
+    L.lb_mlp_destroy.restype = None
+    L.lb_set_mlp.argtypes = [P, P, ctypes.c_int32, ctypes.c_float, ctypes.c_float]
+    L.lb_learned_map_now.argtypes = [P]
+    L.lb_map_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), dp]
     return L
 
 
@@ -218,6 +235,71 @@ def lb_reduce_fields_noalloc(rho_ptr, ux_ptr, uy_ptr, n, restart=False, stream=N
     _check(_lib.lb_reduce_fields_noalloc(ctypes.c_void_p(rho_ptr), ctypes.c_void_p(ux_ptr), ctypes.c_void_p(uy_ptr),
                                          int(n), 1 if restart else 0, ctypes.c_void_p(stream or 0), _dp(out)))
     return out
+
+
+# ------------------------------------------------------------ learned map
+
+NPARAM = 4801
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class MLP:
+    """The learned-placement network (include/lb.h). Arrays passed to the methods are
+    CUDA torch tensors (float32); x is [8][n], y is [n]."""
+
+    def __init__(self, params, norm, stream=None, torch_allocator=True):
+        import torch
+        stream = stream or torch.cuda.current_stream()
+        self._alloc = _TorchAllocator(stream) if torch_allocator else None
+        opts = lb_opts()
+        opts.stream = getattr(stream, "cuda_stream", stream)
+        if self._alloc:
+            opts.alloc, opts.free = self._alloc.alloc, self._alloc.free
+        self._opts = opts
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        nm = np.ascontiguousarray(norm, dtype=np.float32)
+        assert p.size == NPARAM and nm.size == 16
+        self.ptr = ctypes.c_void_p()
+        _check(_lib.lb_mlp_create(_fp(p), _fp(nm), ctypes.byref(opts), ctypes.byref(self.ptr)))
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            _lib.lb_mlp_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def grad(self, x, y):
+        g = np.zeros(NPARAM, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(_lib.lb_mlp_grad(self.ptr, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), y.numel(),
+                                _fp(g), ctypes.byref(loss)))
+        return g, loss.value
+
+    def adam_step(self, x, y, lr=1e-3):
+        _check(_lib.lb_mlp_adam_step(self.ptr, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                     y.numel(), lr))
+
+    def train(self, x, y, epochs=20, batch=256, lr=1e-3, seed=1007):
+        loss = ctypes.c_double()
+        _check(_lib.lb_mlp_train(self.ptr, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), y.numel(),
+                                 epochs, batch, lr, seed, ctypes.byref(loss)))
+        return loss.value
+
+    def params(self):
+        p = np.zeros(NPARAM, dtype=np.float32)
+        _check(_lib.lb_mlp_get_params(self.ptr, _fp(p)))
+        return p
+
+    def infer(self, x, out):
+        _check(_lib.lb_mlp_infer(self.ptr, ctypes.c_void_p(x.data_ptr()), out.numel(), ctypes.c_void_p(out.data_ptr())))
 
 
 # ----------------------------------------------------------------- Lattice
@@ -358,6 +440,26 @@ class Lattice:
 
     def info(self):
         return lb_info(self.ctx)
+
+    def features_into(self, tensor):
+        """Asynchronous: learned-placement features into a CUDA float32 tensor [8][ny][nx]."""
+        _check(_lib.lb_features(self.ctx, ctypes.c_void_p(tensor.data_ptr())))
+
+    def hermite_residual_into(self, tensor):
+        """Asynchronous: ||f - P2 f|| / rho per node into a CUDA float32 tensor [ny][nx]."""
+        _check(_lib.lb_hermite_residual(self.ctx, ctypes.c_void_p(tensor.data_ptr())))
+
+    def set_mlp(self, mlp, every=100, p_on=0.5, p_off=0.3):
+        self._mlp = mlp
+        _check(_lib.lb_set_mlp(self.ctx, mlp.ptr if mlp else None, every, p_on, p_off))
+
+    def learned_map_now(self):
+        _check(_lib.lb_learned_map_now(self.ctx))
+
+    def map_stats(self):
+        u, f, h = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        _check(_lib.lb_map_stats(self.ctx, ctypes.byref(u), ctypes.byref(f), ctypes.byref(h)))
+        return {"updates": u.value, "fallbacks": f.value, "high_fraction": h.value}
 
     def sync(self):
         return lb_sync(self.ctx)

@@ -20,6 +20,7 @@
 
 #include "../../include/lb.h"
 #include "lb_internal.h"
+#include "lb_mlp.h"
 #include "lb_tma.h"
 
 namespace lbq {
@@ -85,6 +86,12 @@ struct lb_ctx {
     bool tma_ok = false;            /* tensor maps built (FP32 / FP16 / BF16 storage) */
     TmaMaps maps[2];                /* per time level */
     int *d_err = nullptr;           /* bounded device waits that ran out */
+    /* learned placement */
+    lb_mlp *mlp = nullptr;
+    int mlp_every = 0;
+    float p_on = 0.5f, p_off = 0.3f;
+    float *d_mom = nullptr, *d_feat = nullptr, *d_p = nullptr, *d_tp = nullptr;
+    int64_t map_updates = 0, map_fallbacks = 0;
     std::vector<void *> owned;
 };
 
@@ -163,6 +170,7 @@ StepParams<R> make_params(const lb_ctx *c, int in, int out, double t_new)
     std::memset(&p, 0, sizeof(p));
     p.nx = c->nx;
     p.ny = c->ny;
+    p.h_grid = c->h;
     p.pitch = c->pitch;
     p.ntx = c->ntx;
     p.tmap = c->d_tmap;
@@ -374,6 +382,80 @@ int choose_variant(lb_ctx *c)
     return use_f64(c) ? autotune_t<double>(c) : autotune_t<float>(c);
 }
 
+void *own(lb_ctx *c, size_t bytes);
+
+int ensure_learned_buffers(lb_ctx *c)
+{
+    const size_t N = (size_t)c->nx * c->ny;
+    /* each buffer on its own, so a failed allocation is retried by the next call (what
+     * did succeed stays owned by the context) */
+    if (!c->d_mom) c->d_mom = static_cast<float *>(own(c, 9 * N * sizeof(float)));
+    if (!c->d_feat) c->d_feat = static_cast<float *>(own(c, 8 * N * sizeof(float)));
+    if (!c->d_p) c->d_p = static_cast<float *>(own(c, N * sizeof(float)));
+    if (!c->d_tp) c->d_tp = static_cast<float *>(own(c, (size_t)c->ny * c->ntx * sizeof(float)));
+    if (!c->d_mom || !c->d_feat || !c->d_p || !c->d_tp) return fail(LB_ERR_NOMEM, "device allocation failed");
+    return LB_OK;
+}
+
+template <typename R>
+int features_t(lb_ctx *c, float *dst)
+{
+    StepParams<R> p = make_params<R>(c, c->cur, c->cur, c->t);
+    lbk::launch_moments<R>(c->store, p, LB_M_ALL, c->d_mom, 0, c->stream);
+    lbk::launch_features<R>(p, c->d_mom, dst, c->stream);
+    return launch_check(c, "features");
+}
+
+int features(lb_ctx *c, float *dst)
+{
+    if (int e = ensure_learned_buffers(c)) return e;
+    return use_f64(c) ? features_t<double>(c, dst) : features_t<float>(c, dst);
+}
+
+int set_region_map_impl(lb_ctx *c, const uint8_t *map);
+
+/* Learned placement: p for every node, its maximum per tile, then a tile turns
+ * high-order at p >= p_on and back to low-order at p < p_off (hysteresis); the two rows
+ * next to each diffuse wall stay high-order. Any non-finite p keeps the current map. */
+int learned_update(lb_ctx *c)
+{
+    /* allocate first: the feature buffer is the destination passed below */
+    if (int e = ensure_learned_buffers(c)) return e;
+    if (int e = features(c, c->d_feat)) return e;
+    const int64_t N = (int64_t)c->nx * c->ny;
+    if (int e = lbk::mlp_infer_dev(c->mlp, c->d_feat, N, c->d_p, c->stream)) return e;
+    lbk::launch_tile_max(c->d_p, c->nx, c->ny, c->ntx, c->d_tp, c->stream);
+    if (int e = launch_check(c, "learned map")) return e;
+    std::vector<float> tp((size_t)c->ny * c->ntx);
+    if (int e = cuda_check(c, cudaMemcpyAsync(tp.data(), c->d_tp, tp.size() * sizeof(float), cudaMemcpyDeviceToHost,
+                                              c->stream), "learned map copy"))
+        return e;
+    if (int e = cuda_check(c, cudaStreamSynchronize(c->stream), "learned map sync")) return e;
+    for (float v : tp)
+        if (!std::isfinite(v)) {
+            c->map_fallbacks += 1;
+            return LB_OK;
+        }
+    std::vector<uint8_t> cell((size_t)N);
+    bool changed = false;
+    for (int j = 0; j < c->ny; ++j) {
+        const bool wall_band = (c->walls[0].kind == LB_WALL_DIFFUSE && j < 2) ||
+                               (c->walls[1].kind == LB_WALL_DIFFUSE && j > c->ny - 3);
+        for (int tx = 0; tx < c->ntx; ++tx) {
+            const size_t k = (size_t)j * c->ntx + tx;
+            const int cur = c->tmap[k] & LB_TILE_HIGH;
+            int nw = cur ? (tp[k] >= c->p_off) : (tp[k] >= c->p_on);
+            if (wall_band) nw = 1;
+            changed = changed || (nw != cur);
+            for (int x = tx * LB_TILE_X; x < std::min(c->nx, (tx + 1) * LB_TILE_X); ++x)
+                cell[(size_t)j * c->nx + x] = (uint8_t)nw;
+        }
+    }
+    c->map_updates += 1;
+    if (!changed) return LB_OK;
+    return set_region_map_impl(c, cell.data());
+}
+
 template <typename R>
 int step_t(lb_ctx *c, int64_t n)
 {
@@ -398,6 +480,8 @@ int step_t(lb_ctx *c, int64_t n)
             cudaEventRecord(c->red_event, c->stream);
             c->red_pending = true;
         }
+        if (c->mlp && c->mlp_every > 0 && c->step % c->mlp_every == 0)
+            if (int e = learned_update(c)) return e;
     }
     return LB_OK;
 }
@@ -766,6 +850,56 @@ int lb_set_region_map(lb_ctx *c, const uint8_t *map)
 {
     if (int e = sticky(c)) return e;
     if (!map) return fail(LB_ERR_INVALID, "null map");
+    return set_region_map_impl(c, map);
+}
+
+int lb_features(lb_ctx *c, float *dst)
+{
+    if (int e = sticky(c)) return e;
+    if (!dst) return fail(LB_ERR_INVALID, "null destination");
+    return features(c, dst);
+}
+
+int lb_hermite_residual(lb_ctx *c, float *dst)
+{
+    if (int e = sticky(c)) return e;
+    if (!dst) return fail(LB_ERR_INVALID, "null destination");
+    if (use_f64(c)) {
+        StepParams<double> p = make_params<double>(c, c->cur, c->cur, c->t);
+        lbk::launch_hermite_residual<double>(c->store, p, dst, c->stream);
+    } else {
+        StepParams<float> p = make_params<float>(c, c->cur, c->cur, c->t);
+        lbk::launch_hermite_residual<float>(c->store, p, dst, c->stream);
+    }
+    return launch_check(c, "hermite residual");
+}
+
+int lb_set_mlp(lb_ctx *c, lb_mlp *m, int32_t every, float p_on, float p_off)
+{
+    if (int e = sticky(c)) return e;
+    if (m && (every < 1 || !(p_on > p_off) || !(p_off >= 0.0f) || !(p_on <= 1.0f)))
+        return fail(LB_ERR_INVALID, "lb_set_mlp: need every >= 1 and 0 <= p_off < p_on <= 1");
+    if (m && c->opts.iface != LB_IFACE_HERMITE)
+        return fail(LB_ERR_INVALID, "lb_set_mlp: learned maps need LB_IFACE_HERMITE (any tile layout)");
+    c->mlp = m;
+    c->mlp_every = m ? every : 0;
+    c->p_on = p_on;
+    c->p_off = p_off;
+    return LB_OK;
+}
+
+int lb_learned_map_now(lb_ctx *c)
+{
+    if (int e = sticky(c)) return e;
+    if (!c->mlp) return fail(LB_ERR_INVALID, "no network set (lb_set_mlp)");
+    return learned_update(c);
+}
+
+}  // extern "C"
+
+namespace {
+int set_region_map_impl(lb_ctx *c, const uint8_t *map)
+{
     std::vector<uint8_t> tm;
     std::vector<int> rows;
     if (int e = build_tiles(c, map, tm, rows)) return e;
@@ -791,6 +925,9 @@ int lb_set_region_map(lb_ctx *c, const uint8_t *map)
     if (int e = finalize_level(c, c->cur)) return e;
     return cuda_check(c, cudaStreamSynchronize(c->stream), "remap sync");
 }
+}  // namespace
+
+extern "C" {
 
 int lb_get_populations(lb_ctx *c, int32_t set, double *dst)
 {
@@ -920,6 +1057,22 @@ int lb_load(lb_ctx *c, const char *path)
     if (int e = lb_state_load(c, buf.data(), bytes)) return e;
     c->step = hd.step;
     c->t = hd.t;
+    return LB_OK;
+}
+
+int lb_map_stats(lb_ctx *c, int64_t *updates, int64_t *fallbacks, double *high_fraction)
+{
+    if (!c) return fail(LB_ERR_INVALID, "null context");
+    if (updates) *updates = c->map_updates;
+    if (fallbacks) *fallbacks = c->map_fallbacks;
+    if (high_fraction) {
+        int64_t hi = 0;
+        for (int j = 0; j < c->ny; ++j)
+            for (int tx = 0; tx < c->ntx; ++tx)
+                if (c->tmap[(size_t)j * c->ntx + tx] & LB_TILE_HIGH)
+                    hi += std::min(c->nx, (tx + 1) * LB_TILE_X) - tx * LB_TILE_X;
+        *high_fraction = (double)hi / ((double)c->nx * c->ny);
+    }
     return LB_OK;
 }
 

@@ -183,6 +183,93 @@ __global__ void reduce_kernel(const __grid_constant__ StepParams<typename Store<
     }
 }
 
+/* Features of the learned placement, from moment fields m [9][ny][nx] (rho, u,
+ * P_xy, Pi^neq xx / xy / yy, q): Pi^neq / rho (3), q / rho (2), wall distance / H,
+ * local Kn = tau (Eq. (KN), without the dt / 2 shift) and Kn |grad rho| / rho with
+ * central differences (one-sided at non-periodic edges). out [8][ny][nx]. */
+template <typename R>
+__global__ void features_kernel(const StepParams<R> p, const float *m, float *out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (x >= p.nx) return;
+    const size_t N = (size_t)p.nx * p.ny, n = (size_t)j * p.nx + x;
+    const float rho = m[n];
+    auto rho_at = [&](int xx, int jj) -> float {
+        if (p.periodic_x) xx = (xx + p.nx) % p.nx;
+        if (p.periodic_y) jj = (jj + p.ny) % p.ny;
+        return m[(size_t)jj * p.nx + xx];
+    };
+    const float h = (float)p.h_grid;
+    float gx, gy;
+    {
+        const bool lo = !p.periodic_x && x == 0, hi = !p.periodic_x && x == p.nx - 1;
+        const int xa = lo ? x : x - 1, xb = hi ? x : x + 1;
+        gx = (rho_at(xb, j) - rho_at(xa, j)) / (h * (float)(xb - xa));
+    }
+    {
+        const bool lo = !p.periodic_y && j == 0, hi = !p.periodic_y && j == p.ny - 1;
+        const int ja = lo ? j : j - 1, jb = hi ? j : j + 1;
+        gy = (rho_at(x, jb) - rho_at(x, ja)) / (h * (float)(jb - ja));
+    }
+    const float kn = p.tau_const ? (float)p.kn_rho : (float)p.kn_rho / rho;
+    float dw = 1.0f;
+    if (p.wall_diffuse[0] || p.wall_diffuse[1]) {
+        const int d0 = p.wall_diffuse[0] ? j : 1 << 30, d1 = p.wall_diffuse[1] ? p.ny - 1 - j : 1 << 30;
+        dw = (float)min(d0, d1) * h;
+    }
+    const float inv = 1.0f / rho;
+    out[0 * N + n] = m[4 * N + n] * inv;
+    out[1 * N + n] = m[5 * N + n] * inv;
+    out[2 * N + n] = m[6 * N + n] * inv;
+    out[3 * N + n] = m[7 * N + n] * inv;
+    out[4 * N + n] = m[8 * N + n] * inv;
+    out[5 * N + n] = dw;
+    out[6 * N + n] = kn;
+    out[7 * N + n] = kn * sqrtf(gx * gx + gy * gy) * inv;
+}
+
+/* Part of a node's populations beyond a second-order Hermite expansion (what a
+ * low-order node cannot hold, Sec. 2.2), per unit mass: ||f - P2 f|| / rho in the norm
+ * sum_a g_a^2 / w_a, from the node's own set. With f = w (rho0 + d) the norm is
+ * sum_a w_a (d_a - d2_a)^2. out [ny][nx]. */
+template <int ST>
+__global__ void hermite_residual_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p, float *out)
+{
+    using T = typename Store<ST>::T;
+    using R = typename Store<ST>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (x >= p.nx) return;
+    const int s = p.tmap[(size_t)j * p.ntx + x / LB_TILE_X] & LB_TILE_HIGH;
+    const SetConst<R> &c = p.set[s];
+    const T *f = static_cast<const T *>(p.fin[s]) + (size_t)j * p.pitch + x + LB_GHOST;
+    R d[LB_QMAX], h[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    for (int a = 0; a < c.q; ++a) {
+        d[a] = decode<ST>(f[a * p.plane], c.winv[a], p.rho0);
+        hermite_acc(c, a, d[a], h);
+    }
+    R num = R(0);
+    for (int a = 0; a < c.q; ++a) {
+        const R e2 = d[a] - hermite_rebuild(c, a, h);
+        num = fma(c.w[a] * e2, e2, num);
+    }
+    out[(size_t)j * p.nx + x] = (float)(sqrt(num) / (p.rho0 + h[0]));
+}
+
+/* Largest p over each map tile (NaN if any node's p is NaN). */
+__global__ void tile_max_kernel(const float *p, int nx, int ny, int ntx, float *out)
+{
+    const int tx = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (tx >= ntx) return;
+    float mx = -1.0f;
+    bool bad = false;
+    for (int x = tx * LB_TILE_X; x < min(nx, (tx + 1) * LB_TILE_X); ++x) {
+        const float v = p[(size_t)j * nx + x];
+        if (!(v == v)) bad = true;
+        mx = fmaxf(mx, v);
+    }
+    out[(size_t)j * ntx + tx] = bad ? nanf("") : mx;
+}
+
 #define LB_DISPATCH(store, ...)                                   \
     switch (store) {                                               \
         case 0: { constexpr int ST = 0; __VA_ARGS__; } break;             \
@@ -236,6 +323,32 @@ void launch_moments(int store, const StepParams<R> &p, uint32_t mask, void *dst,
                                moments_kernel<ST, float><<<grid, 128, 0, st>>>(p, mask, static_cast<float *>(dst)));
     }
 }
+
+template <typename R>
+void launch_features(const StepParams<R> &p, const float *moments, float *out, void *stream)
+{
+    dim3 grid((p.nx + 127) / 128, p.ny);
+    features_kernel<R><<<grid, 128, 0, static_cast<cudaStream_t>(stream)>>>(p, moments, out);
+}
+
+template <typename R>
+void launch_hermite_residual(int store, const StepParams<R> &p, float *out, void *stream)
+{
+    dim3 grid((p.nx + 127) / 128, p.ny);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) hermite_residual_kernel<ST><<<grid, 128, 0, st>>>(p, out));
+}
+
+void launch_tile_max(const float *pr, int nx, int ny, int ntx, float *out, void *stream)
+{
+    dim3 grid((ntx + 63) / 64, ny);
+    tile_max_kernel<<<grid, 64, 0, static_cast<cudaStream_t>(stream)>>>(pr, nx, ny, ntx, out);
+}
+
+template void launch_features<float>(const StepParams<float> &, const float *, float *, void *);
+template void launch_features<double>(const StepParams<double> &, const float *, float *, void *);
+template void launch_hermite_residual<float>(int, const StepParams<float> &, float *, void *);
+template void launch_hermite_residual<double>(int, const StepParams<double> &, float *, void *);
 
 int reduce_blocks(int nx, int ny)
 {

@@ -51,6 +51,7 @@ struct SetConst {
 template <typename R>
 struct StepParams {
     int nx, ny, pitch, ntx;
+    double h_grid;                  /* grid spacing h */
     size_t plane;                   /* elements per plane, (ny + 2 LB_GHOST_ROWS) * pitch */
     const uint8_t *tmap;            /* [ny][ntx] tile flags */
     const void *fin[2];             /* planes of the level read, per set */
@@ -103,5 +104,13 @@ template <typename R>
 void launch_reduce(int store, const StepParams<R> &p, R *uprev, double *part, unsigned int *counter,
                    double *out, int nblocks, void *stream);
 int reduce_blocks(int nx, int ny);
+/* learned placement: features [8][ny][nx] from moment fields [9][ny][nx] (float) */
+template <typename R>
+void launch_features(const StepParams<R> &p, const float *moments, float *out, void *stream);
+/* ||f - P2 f|| / rho per node (beyond-second-order Hermite content), [ny][nx] */
+template <typename R>
+void launch_hermite_residual(int store, const StepParams<R> &p, float *out, void *stream);
+/* per-tile maximum of p [ny][nx] -> out [ny][ntx] */
+void launch_tile_max(const float *p, int nx, int ny, int ntx, float *out, void *stream);
 
 }  // namespace lbk
