@@ -8,6 +8,7 @@
  */
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -86,6 +87,12 @@ struct lb_ctx {
     bool tma_ok = false;            /* tensor maps built (FP32 / FP16 / BF16 storage) */
     TmaMaps maps[2];                /* per time level */
     int *d_err = nullptr;           /* bounded device waits that ran out */
+    /* split step: quads left to the one-quad kernel, for register blocks of 1 and 2 rows */
+    std::vector<int2> edge_h[2];
+    int2 *d_edge[2] = {nullptr, nullptr};
+    size_t edge_cap[2] = {0, 0};
+    cudaStream_t edge_stream = nullptr;   /* the edge kernel runs here, overlapping */
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     /* learned placement */
     lb_mlp *mlp = nullptr;
     int mlp_every = 0;
@@ -312,14 +319,59 @@ int finalize_level(lb_ctx *c, int level)
     return use_f64(c) ? finalize_level_t<double>(c, level) : finalize_level_t<float>(c, level);
 }
 
+void *own(lb_ctx *c, size_t bytes);
+
+/* Lists of the quads the plain kernels of the split step leave to the one-quad kernel:
+ * every quad of a 4 x rb block that is not plain as a whole (plain_quad(), shared with
+ * the device), except mode-A interface rows, which no step kernel updates. */
+int build_edge_lists(lb_ctx *c)
+{
+    const bool px = c->walls[2].kind == LB_WALL_PERIODIC, py = c->walls[0].kind == LB_WALL_PERIODIC;
+    const bool pl = c->walls[2].kind == LB_WALL_PRESSURE, ph = c->walls[3].kind == LB_WALL_PRESSURE;
+    for (int v = 0; v < 2; ++v) {
+        const int rb = v + 1;
+        std::vector<int2> &L = c->edge_h[v];
+        L.clear();
+        for (int j0 = 0; j0 < c->ny; j0 += rb)
+            for (int x0 = 0; x0 < c->nx; x0 += 4) {
+                const int tile = x0 / LB_TILE_X;
+                const uint8_t f0 = c->tmap[(size_t)j0 * c->ntx + tile];
+                bool plain = j0 + rb <= c->ny;
+                for (int r = 0; r < rb && plain; ++r) {
+                    const uint8_t fr = c->tmap[(size_t)(j0 + r) * c->ntx + tile];
+                    plain = fr == f0 && lbk::plain_quad(x0, j0 + r, fr, c->nx, c->ny, px, py, pl, ph);
+                }
+                if (plain) continue;
+                for (int r = 0; r < rb && j0 + r < c->ny; ++r)
+                    if (!(c->tmap[(size_t)(j0 + r) * c->ntx + tile] & LB_TILE_IFACE)) L.push_back(make_int2(x0, j0 + r));
+            }
+        if (L.empty()) continue;
+        if (L.size() > c->edge_cap[v]) {
+            const size_t cap = std::max(L.size(), 2 * c->edge_cap[v]);
+            int2 *d = static_cast<int2 *>(own(c, cap * sizeof(int2)));
+            if (!d) return fail(LB_ERR_NOMEM, "device allocation failed");
+            c->d_edge[v] = d;
+            c->edge_cap[v] = cap;
+        }
+        if (int e = cuda_check(c, cudaMemcpyAsync(c->d_edge[v], L.data(), L.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                                  c->stream), "edge list upload"))
+            return e;
+    }
+    return LB_OK;
+}
+
 int upload_tiles(lb_ctx *c)
 {
-    return cuda_check(c, cudaMemcpyAsync(c->d_tmap, c->tmap.data(), c->tmap.size(), cudaMemcpyHostToDevice, c->stream),
-                      "tile map upload");
+    if (int e = cuda_check(c, cudaMemcpyAsync(c->d_tmap, c->tmap.data(), c->tmap.size(), cudaMemcpyHostToDevice,
+                                              c->stream), "tile map upload"))
+        return e;
+    return build_edge_lists(c);
 }
 
 /* variant 0: one node quad per thread (lb_step_impl.cuh); 1: TMA-fed producer /
- * consumer blocks (lb_step3.cu, not for FP64 storage). */
+ * consumer blocks (lb_step3.cu, not for FP64 storage); 2, 3: split step, plain kernel
+ * on 4 x 1 or 4 x 2 register blocks plus the one-quad kernel on the edge list
+ * (lb_step_impl.cuh). */
 template <typename R>
 void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
 {
@@ -327,7 +379,29 @@ void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
         if (variant == 1 && c->tma_ok && lbk::launch_step3(c->store, p, c->maps[c->cur], c->d_err, c->stream) == 0)
             return;
     }
+    if (variant == 2 || variant == 3) {
+        const int v = variant - 2;
+        const int n = (int)c->edge_h[v].size();
+        if (n > 0) {
+            cudaEventRecord(c->ev_fork, c->stream);
+            cudaStreamWaitEvent(c->edge_stream, c->ev_fork, 0);
+        }
+        lbk::launch_step_split<R>(c->store, p, v + 1, c->d_edge[v], n, c->stream, c->edge_stream);
+        if (n > 0) {
+            cudaEventRecord(c->ev_join, c->edge_stream);
+            cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+        }
+        return;
+    }
     lbk::launch_step<R>(c->store, p, c->stream);
+}
+
+/* layouts this context can run */
+bool variant_available(const lb_ctx *c, int v)
+{
+    if (v == 1) return c->tma_ok;
+    if (v == 2 || v == 3) return c->edge_stream != nullptr;
+    return v >= 0 && v < LB_NUM_VARIANTS;
 }
 
 /* Autotuner: times every step-kernel layout on this lattice (reading the current level,
@@ -348,16 +422,16 @@ int autotune_t(lb_ctx *c)
         auto it = g_tune.find(key);
         if (it != g_tune.end()) return it->second;
     }
-    const int nvar = c->tma_ok ? LB_NUM_VARIANTS : 1;
     StepParams<R> p = make_params<R>(c, c->cur, c->cur ^ 1, c->t + c->dt);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
-        return 1;
+        return 0;
     }
-    int best = 1;
+    int best = 0;
     float best_ms = 1e30f;
-    for (int v = 0; v < nvar; ++v) {
+    for (int v = 0; v < LB_NUM_VARIANTS; ++v) {
+        if (!variant_available(c, v)) continue;
         for (int k = 0; k < 2; ++k) launch_variant<R>(c, v, p);
         cudaEventRecord(e0, c->stream);
         for (int k = 0; k < 5; ++k) launch_variant<R>(c, v, p);
@@ -370,7 +444,7 @@ int autotune_t(lb_ctx *c)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (cudaGetLastError() != cudaSuccess) return 1;
+    if (cudaGetLastError() != cudaSuccess) return 0;
     std::lock_guard<std::mutex> g(g_tune_mu);
     g_tune[key] = best;
     return best;
@@ -378,11 +452,10 @@ int autotune_t(lb_ctx *c)
 
 int choose_variant(lb_ctx *c)
 {
-    if (c->opts.variant >= 0) return (c->opts.variant == 1 && !c->tma_ok) ? 0 : c->opts.variant;
+    if (c->opts.variant >= 0) return variant_available(c, c->opts.variant) ? c->opts.variant : 0;
     return use_f64(c) ? autotune_t<double>(c) : autotune_t<float>(c);
 }
 
-void *own(lb_ctx *c, size_t bytes);
 
 int ensure_learned_buffers(lb_ctx *c)
 {
@@ -513,10 +586,14 @@ int sticky(lb_ctx *c)
 void free_all(lb_ctx *c)
 {
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->edge_stream) cudaStreamSynchronize(c->edge_stream);
     for (void *p : c->owned) dev_free(c, p);
     c->owned.clear();
     if (c->h_out) cudaFreeHost(c->h_out);
     if (c->red_event) cudaEventDestroy(c->red_event);
+    if (c->edge_stream) cudaStreamDestroy(c->edge_stream);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
 }
 
 void *own(lb_ctx *c, size_t bytes)
@@ -710,6 +787,18 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
         return fail(LB_ERR_CUDA, "pinned buffer / event creation failed");
     }
     std::memset(c->h_out, 0, 4 * sizeof(double));
+    /* second stream and fork / join events of the split step; without them that layout
+     * is simply not offered */
+    if (cudaStreamCreateWithFlags(&c->edge_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->edge_stream) cudaStreamDestroy(c->edge_stream);
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        if (c->ev_join) cudaEventDestroy(c->ev_join);
+        c->edge_stream = nullptr;
+        c->ev_fork = c->ev_join = nullptr;
+    }
     cudaError_t ce = cudaSuccess;
     for (int lv = 0; lv < 2 && ce == cudaSuccess; ++lv)
         for (int s = 0; s < 2 && ce == cudaSuccess; ++s) ce = cudaMemsetAsync(c->planes[lv][s], 0, c->set_bytes[s], c->stream);

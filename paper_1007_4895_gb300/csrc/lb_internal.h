@@ -82,7 +82,32 @@ namespace lbk {
  * 1 = TMA-fed producer / consumer blocks (lb_step3.cu, FP32 / FP16 / BF16 storage) */
 template <typename R>
 void launch_step(int store, const StepParams<R> &p, void *stream);
-#define LB_NUM_VARIANTS 2
+/* Split form of the step: a plain kernel over the quads for which plain_quad() holds,
+ * in register blocks of 4 x rb nodes (rb = 1 or 2; a block is plain when all its rb
+ * quads are), and the one-quad kernel over the listed remaining quads (x0, j) on
+ * edge_stream, which the caller forks from and joins back into stream. */
+template <typename R>
+void launch_step_split(int store, const StepParams<R> &p, int rb, const int2 *edge, int n_edge, void *stream,
+                       void *edge_stream);
+/* step-kernel layouts: 0 one node quad per thread, 1 TMA-fed producer / consumer,
+ * 2 and 3 split plain / edge kernels with register blocks of 4 x 1 and 4 x 2 nodes */
+#define LB_NUM_VARIANTS 4
+
+/* The quad of nodes x0 .. x0+3 of row j needs none of the boundary work of the step
+ * (wall overwrite, ghost-row or ghost-column copies, pressure column, mode-B shadow or
+ * mode-A interface row): the plain kernels update it, the one-quad kernel the rest.
+ * Host and device share this one definition. */
+__host__ __device__ inline bool plain_quad(int x0, int j, uint8_t flags, int nx, int ny, bool periodic_x,
+                                           bool periodic_y, bool pressure_lo, bool pressure_hi)
+{
+    if (flags & (LB_TILE_SHADOW | LB_TILE_IFACE)) return false;
+    if (periodic_y ? (j < 2 || j >= ny - 2) : (j == 0 || j == ny - 1)) return false;
+    if (x0 + 3 >= nx) return false;
+    if (pressure_lo && x0 == 0) return false;
+    if (pressure_hi && x0 + 3 >= nx - 1) return false;
+    if (periodic_x && (x0 < LB_GHOST || x0 + 3 >= nx - LB_GHOST)) return false;
+    return true;
+}
 template <typename R>
 void launch_iface(int store, const StepParams<R> &p, void *stream);
 template <typename R>

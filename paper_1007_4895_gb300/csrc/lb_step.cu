@@ -13,6 +13,9 @@ namespace lbk {
 
 template <int ST>
 void launch_step_store(const StepParams<typename Store<ST>::R> &p, void *stream);
+template <int ST>
+void launch_step_split_store(const StepParams<typename Store<ST>::R> &p, int rb, const int2 *edge, int n_edge,
+                             void *stream, void *edge_stream);
 
 /* ---------------------------------------------------------------- mode A -- */
 
@@ -72,62 +75,88 @@ __global__ void iface_kernel(const __grid_constant__ StepParams<typename Store<S
 
 /* ------------------------------------------------------- pressure columns -- */
 
+/* Sum over the 32 lanes of a warp (every lane gets the total). */
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 /* Column x = 0 (left) or nx-1 (right), interior rows: f = f_eq(rho_b, u_1) +
  * [f - f_eq](node one step inwards), the virtual-boundary construction of Sec. 2.2
  * applied to an open boundary. Then every row's ghost columns beyond the boundary get
  * copies of the boundary node (in its set, and rebuilt in the other set where the tile
- * neighbours it). */
+ * neighbours it). One warp per (row, side); lane l handles populations l and l + 32, and
+ * the node sums are warp reductions. */
 template <int ST>
 __global__ void pressure_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p)
 {
     using T = typename Store<ST>::T;
     using R = typename Store<ST>::R;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int side = blockIdx.y;
-    if (j >= p.ny || !p.pressure[side]) return;
+    if (j >= p.ny || !p.pressure[side]) return;   /* uniform over the warp */
     const int xb = side == 0 ? 0 : p.nx - 1;
     const int xi = side == 0 ? 1 : p.nx - 2;
     const uint8_t flags = p.tmap[(size_t)j * p.ntx + xb / LB_TILE_X];
     const int s = flags & LB_TILE_HIGH;
     const SetConst<R> &c = p.set[s];
+    const int q = c.q;
     const size_t plane = p.plane;
     const R rho0 = p.rho0;
     T *f = static_cast<T *>(p.fout[s]) + (size_t)j * p.pitch + LB_GHOST;
-    R dv[LB_QMAX];
+    const int a0 = lane, a1 = lane + 32;
+    const bool h0 = a0 < q, h1 = a1 < q;
+    int img[2];
+    const int nimg = row_images(p, j, img);
     if (is_pressure_node(p, xb, j)) {
-        R r = R(0), mx = R(0), my = R(0);
-        for (int a = 0; a < c.q; ++a) {
-            dv[a] = decode<ST>(f[a * plane + xi], c.winv[a], rho0);
-            r = fma(c.w[a], dv[a], r);
-            mx = fma(c.wcx[a], dv[a], mx);
-            my = fma(c.wcy[a], dv[a], my);
+        R d0 = R(0), d1 = R(0), r = R(0), mx = R(0), my = R(0);
+        if (h0) {
+            d0 = decode<ST>(f[a0 * plane + xi], c.winv[a0], rho0);
+            r = c.w[a0] * d0;
+            mx = c.wcx[a0] * d0;
+            my = c.wcy[a0] * d0;
         }
+        if (h1) {
+            d1 = decode<ST>(f[a1 * plane + xi], c.winv[a1], rho0);
+            r = fma(c.w[a1], d1, r);
+            mx = fma(c.wcx[a1], d1, mx);
+            my = fma(c.wcy[a1], d1, my);
+        }
+        r = warp_sum(r);
+        mx = warp_sum(mx);
+        my = warp_sum(my);
         const R rn = rho0 + r, uxn = mx / rn, uyn = my / rn, usn = uxn * uxn + uyn * uyn;
         const R rb = p.rho_side[side];
-        int img[2];
-        const int nimg = row_images(p, j, img);
-        for (int a = 0; a < c.q; ++a) {
+        auto put = [&](int a, R d) {
             const R e = c.cx[a] * uxn + c.cy[a] * uyn;
-            dv[a] = deq(rb - rho0, rb, e, usn) + (dv[a] - deq(r, rn, e, usn));
-            const T v = encode<ST>(dv[a], c.w[a], rho0);
+            const R dv = deq(rb - rho0, rb, e, usn) + (d - deq(r, rn, e, usn));
+            const T v = encode<ST>(dv, c.w[a], rho0);
             f[a * plane + xb] = v;
             for (int t = 0; t < nimg; ++t) f[a * plane + (ptrdiff_t)img[t] * p.pitch + xb] = v;
-        }
+        };
+        if (h0) put(a0, d0);
+        if (h1) put(a1, d1);
     }
-    for (int a = 0; a < c.q; ++a) {
+    /* ghost columns, and the node's second-order Hermite coefficients for a shadow */
+    R hc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    auto ghost = [&](int a) {
         const T e = f[a * plane + xb];
-        dv[a] = decode<ST>(e, c.winv[a], rho0);
         for (int g = 1; g <= LB_GHOST; ++g) f[a * plane + (side == 0 ? xb - g : xb + g)] = e;
-    }
+        hermite_acc(c, a, decode<ST>(e, c.winv[a], rho0), hc);
+    };
+    if (h0) ghost(a0);
+    if (h1) ghost(a1);
     if (flags & LB_TILE_SHADOW) {
-        R h[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-        for (int a = 0; a < c.q; ++a) hermite_acc(c, a, dv[a], h);
+#pragma unroll
+        for (int m = 0; m < 6; ++m) hc[m] = warp_sum(hc[m]);
         const SetConst<R> &ct = p.set[1 - s];
         T *ft = static_cast<T *>(p.fout[1 - s]) + (size_t)j * p.pitch + LB_GHOST;
-        int img[2];
-        const int nimg = row_images(p, j, img);
-        for (int b = 0; b < ct.q; ++b) {
-            const T e = encode<ST>(hermite_rebuild(ct, b, h), ct.w[b], rho0);
+        for (int b = lane; b < ct.q; b += 32) {
+            const T e = encode<ST>(hermite_rebuild(ct, b, hc), ct.w[b], rho0);
             for (int g = 0; g <= LB_GHOST; ++g) ft[b * plane + (side == 0 ? xb - g : xb + g)] = e;
             for (int t = 0; t < nimg; ++t) ft[b * plane + (ptrdiff_t)img[t] * p.pitch + xb] = e;
         }
@@ -187,6 +216,14 @@ void launch_step(int store, const StepParams<R> &p, void *stream)
 }
 
 template <typename R>
+void launch_step_split(int store, const StepParams<R> &p, int rb, const int2 *edge, int n_edge, void *stream,
+                       void *edge_stream)
+{
+    LB_DISPATCH(store, if constexpr (store_matches<R, ST>())
+                           launch_step_split_store<ST>(p, rb, edge, n_edge, stream, edge_stream));
+}
+
+template <typename R>
 void launch_iface(int store, const StepParams<R> &p, void *stream)
 {
     if (p.n_iface <= 0) return;
@@ -199,9 +236,9 @@ template <typename R>
 void launch_pressure(int store, const StepParams<R> &p, void *stream)
 {
     if (!p.pressure[0] && !p.pressure[1]) return;
-    dim3 grid((p.ny + 63) / 64, 2);
+    dim3 grid((p.ny + 3) / 4, 2);   /* four warps (rows) per block */
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) pressure_kernel<ST><<<grid, 64, 0, st>>>(p));
+    LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) pressure_kernel<ST><<<grid, 128, 0, st>>>(p));
 }
 
 template <typename R>
@@ -214,6 +251,8 @@ void launch_shadows(int store, const StepParams<R> &p, void *stream)
 
 template void launch_step<float>(int, const StepParams<float> &, void *);
 template void launch_step<double>(int, const StepParams<double> &, void *);
+template void launch_step_split<float>(int, const StepParams<float> &, int, const int2 *, int, void *, void *);
+template void launch_step_split<double>(int, const StepParams<double> &, int, const int2 *, int, void *, void *);
 template void launch_iface<float>(int, const StepParams<float> &, void *);
 template void launch_iface<double>(int, const StepParams<double> &, void *);
 template void launch_pressure<float>(int, const StepParams<float> &, void *);

@@ -80,7 +80,17 @@ __device__ __forceinline__ void x_flux_diff(R c, R kf, const R l[2], const R v[4
     }
 }
 
-template <int ST, int Q>
+/* Stored values one population needs for a quad: its own four, two beside them on each
+ * side (x flux, when xi_x != 0) and three rows on the upwind / downwind sides (y flux,
+ * when xi_y != 0: rows j-2, j-1, j+1 for xi_y > 0, rows j-1, j+1, j+2 for xi_y < 0). */
+template <typename T>
+struct QuadStencil {
+    T v[4], l[2], r[2], y0[4], y1[4], y2[4];
+};
+
+/* PF: load population a + 1 while population a is computed (one-deep software
+ * pipeline), for kernels whose threads are few and latency-bound. */
+template <int ST, int Q, bool PF = false>
 __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::R> &p, int s, uint8_t flags, int x0,
                                            int j, const PopC<typename Store<ST>::R> *pcs,
                                            const MomC<typename Store<ST>::R> *mcs)
@@ -160,85 +170,185 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
         }
     };
 
-    /* 3. stencil, fluxes, collision, force */
+    /* 3. stencil, fluxes, collision, force (PF: loads one population ahead) */
     R num[4] = {R(0), R(0), R(0), R(0)};
-#pragma unroll 1
-    for (int a = 0; a < Q; ++a) {
-        const T *pa = fin + a * plane + row0;
-        const PopC<R> pc = pcs[a];
-        const R winv = pc.winv;
-        T raw[4];
-        R v[4], l[2], r[2];
-        ld4(pa, raw);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = decode<ST>(raw[k], winv, rho0);
-        R Dx[4], Dy[4];
-        const R crx = pc.crx, cry = pc.cry;
-        if (crx != R(0)) {
-            T tl[2], tr[2];
-            ld2(pa - 2, tl);
-            ld2(pa + 4, tr);
-            l[0] = decode<ST>(tl[0], winv, rho0);
-            l[1] = decode<ST>(tl[1], winv, rho0);
-            r[0] = decode<ST>(tr[0], winv, rho0);
-            r[1] = decode<ST>(tr[1], winv, rho0);
-        }
-        x_flux_diff(crx, pc.kx, l, v, r, Dx);
-        if (cry > R(0)) {
-            T t2[4], t1[4], tp[4];
-            ld4(pa + om2, t2);
-            ld4(pa + om1, t1);
-            ld4(pa + op1, tp);
-            const R kf = pc.ky;
-#pragma unroll
+    if constexpr (!PF) {
+    #pragma unroll 1
+        for (int a = 0; a < Q; ++a) {
+            const T *pa = fin + a * plane + row0;
+            const PopC<R> pc = pcs[a];
+            const R winv = pc.winv;
+            T raw[4];
+            R v[4], l[2], r[2];
+            ld4(pa, raw);
+    #pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = decode<ST>(raw[k], winv, rho0);
+            R Dx[4], Dy[4];
+            const R crx = pc.crx, cry = pc.cry;
+            if (crx != R(0)) {
+                T tl[2], tr[2];
+                ld2(pa - 2, tl);
+                ld2(pa + 4, tr);
+                l[0] = decode<ST>(tl[0], winv, rho0);
+                l[1] = decode<ST>(tl[1], winv, rho0);
+                r[0] = decode<ST>(tr[0], winv, rho0);
+                r[1] = decode<ST>(tr[1], winv, rho0);
+            }
+            x_flux_diff(crx, pc.kx, l, v, r, Dx);
+            if (cry > R(0)) {
+                T t2[4], t1[4], tp[4];
+                ld4(pa + om2, t2);
+                ld4(pa + om1, t1);
+                ld4(pa + op1, tp);
+                const R kf = pc.ky;
+    #pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    R ym2 = decode<ST>(t2[k], winv, rho0), ym1 = decode<ST>(t1[k], winv, rho0);
+                    R yp1 = decode<ST>(tp[k], winv, rho0);
+                    R d0 = ym1 - ym2, d1 = v[k] - ym1, d2 = yp1 - v[k];
+                    const R n1 = neg_part(d1);
+                    Dy[k] = fma(kf, minmod_n(d1, d2, n1, neg_part(d2)) - minmod_n(d0, d1, neg_part(d0), n1), d1);
+                }
+            } else if (cry < R(0)) {
+                T t1[4], tp[4], t2[4];
+                ld4(pa + om1, t1);
+                ld4(pa + op1, tp);
+                ld4(pa + op2, t2);
+                const R kf = pc.ky;
+    #pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    R ym1 = decode<ST>(t1[k], winv, rho0), yp1 = decode<ST>(tp[k], winv, rho0);
+                    R yp2 = decode<ST>(t2[k], winv, rho0);
+                    R e0 = v[k] - ym1, e1 = yp1 - v[k], e2 = yp2 - yp1;
+                    const R n1 = neg_part(e1);
+                    Dy[k] = fma(-kf, minmod_n(e1, e2, n1, neg_part(e2)) - minmod_n(e0, e1, neg_part(e0), n1), e1);
+                }
+            } else {
+    #pragma unroll
+                for (int k = 0; k < 4; ++k) Dy[k] = R(0);
+            }
+            R dn[4];
+            const R cxa = pc.cx, cya = pc.cy;
+            const R gxi = p.gx * cxa + p.gy * cya;
+    #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                R ym2 = decode<ST>(t2[k], winv, rho0), ym1 = decode<ST>(t1[k], winv, rho0);
-                R yp1 = decode<ST>(tp[k], winv, rho0);
-                R d0 = ym1 - ym2, d1 = v[k] - ym1, d2 = yp1 - v[k];
-                const R n1 = neg_part(d1);
-                Dy[k] = fma(kf, minmod_n(d1, d2, n1, neg_part(d2)) - minmod_n(d0, d1, neg_part(d0), n1), d1);
+                R eu = cxa * ux[k] + cya * uy[k];
+                R de = deq(rhod[k], rho[k], eu, usq[k]);
+                /* sum the small increments first and round onto the stored magnitude once */
+                R inc = om[k] * (de - v[k]);
+                inc = fma(-crx, Dx[k], inc);
+                inc = fma(-cry, Dy[k], inc);
+                if (p.has_force) inc = fma(p.dt * rho[k], gxi + gxi * eu - gu[k], inc);
+                dn[k] = v[k] + inc;
             }
-        } else if (cry < R(0)) {
-            T t1[4], tp[4], t2[4];
-            ld4(pa + om1, t1);
-            ld4(pa + op1, tp);
-            ld4(pa + op2, t2);
-            const R kf = pc.ky;
-#pragma unroll
+            if (wall >= 0) {
+                const R xn = cya * nsgn;
+                if (xn > R(0)) continue;   /* replaced below */
+                if (xn < R(0)) {
+    #pragma unroll
+                    for (int k = 0; k < 4; ++k) num[k] = fma(-xn * pc.w, dn[k], num[k]);
+                }
+            }
+            store_quad(fout + a * plane + row0, dn, pc.w);
+        }
+
+    } else {
+        auto load = [&](int a, QuadStencil<T> &S, PopC<R> &pc) {
+            pc = pcs[a];
+            const T *pa = fin + a * plane + row0;
+            ld4(pa, S.v);
+            if (pc.crx != R(0)) {
+                ld2(pa - 2, S.l);
+                ld2(pa + 4, S.r);
+            }
+            if (pc.cry > R(0)) {
+                ld4(pa + om2, S.y0);
+                ld4(pa + om1, S.y1);
+                ld4(pa + op1, S.y2);
+            } else if (pc.cry < R(0)) {
+                ld4(pa + om1, S.y0);
+                ld4(pa + op1, S.y1);
+                ld4(pa + op2, S.y2);
+            }
+        };
+        QuadStencil<T> cur, nxt;
+        PopC<R> pcur, pnxt;
+        if constexpr (PF) load(0, cur, pcur);
+    #pragma unroll 1
+        for (int a = 0; a < Q; ++a) {
+            if constexpr (PF) {
+                if (a + 1 < Q) load(a + 1, nxt, pnxt);
+            } else {
+                load(a, cur, pcur);
+            }
+            const PopC<R> pc = pcur;
+            const R winv = pc.winv;
+            R v[4], l[2], r[2];
+    #pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = decode<ST>(cur.v[k], winv, rho0);
+            R Dx[4], Dy[4];
+            const R crx = pc.crx, cry = pc.cry;
+            if (crx != R(0)) {
+                l[0] = decode<ST>(cur.l[0], winv, rho0);
+                l[1] = decode<ST>(cur.l[1], winv, rho0);
+                r[0] = decode<ST>(cur.r[0], winv, rho0);
+                r[1] = decode<ST>(cur.r[1], winv, rho0);
+            }
+            x_flux_diff(crx, pc.kx, l, v, r, Dx);
+            if (cry > R(0)) {
+                const R kf = pc.ky;
+    #pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    R ym2 = decode<ST>(cur.y0[k], winv, rho0), ym1 = decode<ST>(cur.y1[k], winv, rho0);
+                    R yp1 = decode<ST>(cur.y2[k], winv, rho0);
+                    R d0 = ym1 - ym2, d1 = v[k] - ym1, d2 = yp1 - v[k];
+                    const R n1 = neg_part(d1);
+                    Dy[k] = fma(kf, minmod_n(d1, d2, n1, neg_part(d2)) - minmod_n(d0, d1, neg_part(d0), n1), d1);
+                }
+            } else if (cry < R(0)) {
+                const R kf = pc.ky;
+    #pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    R ym1 = decode<ST>(cur.y0[k], winv, rho0), yp1 = decode<ST>(cur.y1[k], winv, rho0);
+                    R yp2 = decode<ST>(cur.y2[k], winv, rho0);
+                    R e0 = v[k] - ym1, e1 = yp1 - v[k], e2 = yp2 - yp1;
+                    const R n1 = neg_part(e1);
+                    Dy[k] = fma(-kf, minmod_n(e1, e2, n1, neg_part(e2)) - minmod_n(e0, e1, neg_part(e0), n1), e1);
+                }
+            } else {
+    #pragma unroll
+                for (int k = 0; k < 4; ++k) Dy[k] = R(0);
+            }
+            R dn[4];
+            const R cxa = pc.cx, cya = pc.cy;
+            const R gxi = p.gx * cxa + p.gy * cya;
+    #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                R ym1 = decode<ST>(t1[k], winv, rho0), yp1 = decode<ST>(tp[k], winv, rho0);
-                R yp2 = decode<ST>(t2[k], winv, rho0);
-                R e0 = v[k] - ym1, e1 = yp1 - v[k], e2 = yp2 - yp1;
-                const R n1 = neg_part(e1);
-                Dy[k] = fma(-kf, minmod_n(e1, e2, n1, neg_part(e2)) - minmod_n(e0, e1, neg_part(e0), n1), e1);
+                R eu = cxa * ux[k] + cya * uy[k];
+                R de = deq(rhod[k], rho[k], eu, usq[k]);
+                /* sum the small increments first and round onto the stored magnitude once */
+                R inc = om[k] * (de - v[k]);
+                inc = fma(-crx, Dx[k], inc);
+                inc = fma(-cry, Dy[k], inc);
+                if (p.has_force) inc = fma(p.dt * rho[k], gxi + gxi * eu - gu[k], inc);
+                dn[k] = v[k] + inc;
             }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) Dy[k] = R(0);
-        }
-        R dn[4];
-        const R cxa = pc.cx, cya = pc.cy;
-        const R gxi = p.gx * cxa + p.gy * cya;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            R eu = cxa * ux[k] + cya * uy[k];
-            R de = deq(rhod[k], rho[k], eu, usq[k]);
-            /* sum the small increments first and round onto the stored magnitude once */
-            R inc = om[k] * (de - v[k]);
-            inc = fma(-crx, Dx[k], inc);
-            inc = fma(-cry, Dy[k], inc);
-            if (p.has_force) inc = fma(p.dt * rho[k], gxi + gxi * eu - gu[k], inc);
-            dn[k] = v[k] + inc;
-        }
-        if (wall >= 0) {
-            const R xn = cya * nsgn;
-            if (xn > R(0)) continue;   /* replaced below */
-            if (xn < R(0)) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) num[k] = fma(-xn * pc.w, dn[k], num[k]);
+            bool replaced = false;   /* wall-bound population on a wall row: written below */
+            if (wall >= 0) {
+                const R xn = cya * nsgn;
+                replaced = xn > R(0);
+                if (xn < R(0)) {
+    #pragma unroll
+                    for (int k = 0; k < 4; ++k) num[k] = fma(-xn * pc.w, dn[k], num[k]);
+                }
+            }
+            if (!replaced) store_quad(fout + a * plane + row0, dn, pc.w);
+            if constexpr (PF) {
+                cur = nxt;
+                pcur = pnxt;
             }
         }
-        store_quad(fout + a * plane + row0, dn, pc.w);
+
     }
 
     /* 4. diffuse wall: f_out = rho_W S(u_W) with zero net mass flux through the wall */
@@ -310,6 +420,273 @@ __global__ void __launch_bounds__(LB_BX *LB_BY, ST == 0 ? 2 : LB_MINB) step_kern
     else step_cells<ST, 36>(p, s, flags, x0, j, pc[s], mc[s]);
 }
 
+
+/* ------------------------------------------------------------------------------
+ * Split form: plain quads (plain_quad(): no wall, ghost-copy, pressure, shadow or
+ * interface work) in register blocks of 4 columns x RB rows per thread, with none of
+ * the boundary logic of step_cells, so the kernel needs few registers; the remaining
+ * quads through step_cells from a list. With RB = 2 a population's y stencil is read
+ * once for both rows (RB + 3 rows instead of 3 RB) and the limited face slope between
+ * the two rows is formed once. The arithmetic per node is that of step_cells, in the
+ * same order, so every layout gives the same bits.
+ * ---------------------------------------------------------------------------- */
+
+/* y flux difference of the rows r = 0 .. RB-1 of one column from the RB + 3 rows of
+ * its upwind window W: rows j0-2 .. j0+RB for xi_y > 0 (then kfs = kf), rows
+ * j0-1 .. j0+RB+1 for xi_y < 0 (kfs = -kf, the mirrored flux). With d_i = W_{i+1} - W_i
+ * and the face slope M_i = minmod(d_i, d_{i+1}), D_r = d_{r+1} + kfs (M_{r+1} - M_r):
+ * each face slope is formed once for the two rows beside it. */
+template <typename R, int RB>
+__device__ __forceinline__ void y_flux_window(R kfs, const R (&W)[RB + 3], R (&D)[RB])
+{
+    R d[RB + 2], n[RB + 2], m[RB + 1];
+#pragma unroll
+    for (int i = 0; i < RB + 2; ++i) {
+        d[i] = W[i + 1] - W[i];
+        n[i] = neg_part(d[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < RB + 1; ++i) m[i] = minmod_n(d[i], d[i + 1], n[i], n[i + 1]);
+#pragma unroll
+    for (int r = 0; r < RB; ++r) D[r] = fma(kfs, m[r + 1] - m[r], d[r + 1]);
+}
+
+/* Stored values one population needs for a 4 x RB block: its own rows, the three rows
+ * beyond them on the two sides (j0-2, j0-1, j0+RB for xi_y > 0; j0-1, j0+RB,
+ * j0+RB+1 for xi_y < 0) and two values beside each own row (when xi_x != 0). */
+template <typename T, int RB>
+struct BlkStencil {
+    T own[RB][4], hy[3][4], l[RB][2], r[RB][2];
+};
+
+template <int ST, int Q, int RB, bool FORCE>
+__device__ __forceinline__ void blk_cells(const StepParams<typename Store<ST>::R> &p, int s, int x0, int j0,
+                                          const PopC<typename Store<ST>::R> *pcs,
+                                          const MomC<typename Store<ST>::R> *mcs)
+{
+    using T = typename Store<ST>::T;
+    using R = typename Store<ST>::R;
+    const size_t plane = p.plane;
+    const ptrdiff_t pitch = p.pitch;
+    const size_t off = (size_t)j0 * pitch + (size_t)(x0 + LB_GHOST);
+    const T *__restrict__ fin = static_cast<const T *>(p.fin[s]) + off;
+    T *__restrict__ fout = static_cast<T *>(p.fout[s]) + off;
+    const R rho0 = p.rho0;
+
+    /* 1. moments of the 4 x RB nodes */
+    R rhod[RB][4], ux[RB][4], uy[RB][4];
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rhod[r][k] = ux[r][k] = uy[r][k] = R(0);
+#pragma unroll 4
+    for (int a = 0; a < Q; ++a) {
+        const MomC<R> mc = mcs[a];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            T raw[4];
+            ld4(fin + a * plane + r * pitch, raw);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const R d = decode<ST>(raw[k], mc.winv, rho0);
+                rhod[r][k] = fma(mc.w, d, rhod[r][k]);
+                ux[r][k] = fma(mc.wcx, d, ux[r][k]);
+                uy[r][k] = fma(mc.wcy, d, uy[r][k]);
+            }
+        }
+    }
+    /* 2. macroscopic state: rho, u, relaxation rate (and force terms) */
+    R rho[RB][4], usq[RB][4], om[RB][4], gu[RB][4];
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            rho[r][k] = rho0 + rhod[r][k];
+            const R inv = R(1) / rho[r][k];
+            ux[r][k] *= inv;
+            uy[r][k] *= inv;
+            usq[r][k] = ux[r][k] * ux[r][k] + uy[r][k] * uy[r][k];
+            om[r][k] = p.dt / tau_of(p, rho[r][k]);
+            if constexpr (FORCE) gu[r][k] = p.gx * ux[r][k] + p.gy * uy[r][k];
+        }
+
+    /* 3. per population: stencil (loaded one population ahead), fluxes, collision,
+     * force, store */
+    auto load = [&](int a, BlkStencil<T, RB> &S, PopC<R> &pc) {
+        pc = pcs[a];
+        const T *pa = fin + a * plane;
+#pragma unroll
+        for (int r = 0; r < RB; ++r) ld4(pa + r * pitch, S.own[r]);
+        if (pc.cry > R(0)) {
+            ld4(pa - 2 * pitch, S.hy[0]);
+            ld4(pa - pitch, S.hy[1]);
+            ld4(pa + RB * pitch, S.hy[2]);
+        } else if (pc.cry < R(0)) {
+            ld4(pa - pitch, S.hy[0]);
+            ld4(pa + RB * pitch, S.hy[1]);
+            ld4(pa + (RB + 1) * pitch, S.hy[2]);
+        }
+        if (pc.crx != R(0)) {
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                ld2(pa + r * pitch - 2, S.l[r]);
+                ld2(pa + r * pitch + 4, S.r[r]);
+            }
+        }
+    };
+    BlkStencil<T, RB> cur, nxt;
+    PopC<R> pcur, pnxt;
+    load(0, cur, pcur);
+#pragma unroll 1
+    for (int a = 0; a < Q; ++a) {
+        if (a + 1 < Q) load(a + 1, nxt, pnxt);
+        const PopC<R> pc = pcur;
+        const R winv = pc.winv, crx = pc.crx, cry = pc.cry;
+        const R cxa = pc.cx, cya = pc.cy;
+        R v[RB][4];
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[r][k] = decode<ST>(cur.own[r][k], winv, rho0);
+        /* collision first, then the x and y flux differences, then the force: the
+         * increments are summed in the order step_cells uses and rounded onto the
+         * stored magnitude once */
+        R inc[RB][4];
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const R eu = cxa * ux[r][k] + cya * uy[r][k];
+                inc[r][k] = om[r][k] * (deq(rhod[r][k], rho[r][k], eu, usq[r][k]) - v[r][k]);
+            }
+        if (crx != R(0)) {
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const R l[2] = {decode<ST>(cur.l[r][0], winv, rho0), decode<ST>(cur.l[r][1], winv, rho0)};
+                const R rr[2] = {decode<ST>(cur.r[r][0], winv, rho0), decode<ST>(cur.r[r][1], winv, rho0)};
+                R Dx[4];
+                x_flux_diff(crx, pc.kx, l, v[r], rr, Dx);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) inc[r][k] = fma(-crx, Dx[k], inc[r][k]);
+            }
+        }
+        if (cry != R(0)) {
+            const bool up = cry > R(0);
+            const R kfs = up ? pc.ky : -pc.ky;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                R W[RB + 3], Dy[RB];
+                const R h0 = decode<ST>(cur.hy[0][k], winv, rho0), h1 = decode<ST>(cur.hy[1][k], winv, rho0);
+                const R h2 = decode<ST>(cur.hy[2][k], winv, rho0);
+                if (up) {
+                    W[0] = h0;
+                    W[1] = h1;
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) W[2 + r] = v[r][k];
+                    W[RB + 2] = h2;
+                } else {
+                    W[0] = h0;
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) W[1 + r] = v[r][k];
+                    W[RB + 1] = h1;
+                    W[RB + 2] = h2;
+                }
+                y_flux_window<R, RB>(kfs, W, Dy);
+#pragma unroll
+                for (int r = 0; r < RB; ++r) inc[r][k] = fma(-cry, Dy[r], inc[r][k]);
+            }
+        }
+        const R gxi = p.gx * cxa + p.gy * cya;
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            T e[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                R t = inc[r][k];
+                if constexpr (FORCE) {
+                    const R eu = cxa * ux[r][k] + cya * uy[r][k];
+                    t = fma(p.dt * rho[r][k], gxi + gxi * eu - gu[r][k], t);
+                }
+                e[k] = encode<ST>(v[r][k] + t, pc.w, rho0);
+            }
+            st4(fout + a * plane + r * pitch, e);
+        }
+        cur = nxt;
+        pcur = pnxt;
+    }
+}
+
+/* Plain kernel of the split step: one thread per 4 x RB block of nodes, which it
+ * updates only when every quad of the block is plain (the rest are listed for the
+ * edge kernel). */
+template <int ST, int RB, bool FORCE>
+__global__ void __launch_bounds__(32 * (8 / RB)) step_plain_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p)
+{
+    using R = typename Store<ST>::R;
+    __shared__ PopC<R> pc[2][LB_QMAX];
+    __shared__ MomC<R> mc[2][LB_QMAX];
+    stage_consts(p, pc, mc, threadIdx.y * 32 + threadIdx.x, 32 * (8 / RB));
+    __syncthreads();
+    const int x0 = (blockIdx.x * 32 + threadIdx.x) * 4;
+    const int j0 = (blockIdx.y * (8 / RB) + threadIdx.y) * RB;
+    if (j0 + RB > p.ny || x0 >= p.nx) return;
+    const int tile = x0 / LB_TILE_X;
+    const uint8_t f0 = p.tmap[(size_t)j0 * p.ntx + tile];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+        const uint8_t fr = r == 0 ? f0 : p.tmap[(size_t)(j0 + r) * p.ntx + tile];
+        if (fr != f0 || !plain_quad(x0, j0 + r, fr, p.nx, p.ny, p.periodic_x, p.periodic_y, p.pressure[0], p.pressure[1]))
+            return;
+    }
+    const int s = f0 & LB_TILE_HIGH;
+    const int q = p.set[s].q;
+    if (q == 9) blk_cells<ST, 9, RB, FORCE>(p, s, x0, j0, pc[s], mc[s]);
+    else if (q == 16) blk_cells<ST, 16, RB, FORCE>(p, s, x0, j0, pc[s], mc[s]);
+    else blk_cells<ST, 36, RB, FORCE>(p, s, x0, j0, pc[s], mc[s]);
+}
+
+/* Edge kernel of the split step: the one-quad path for each listed quad (x0, j). */
+template <int ST>
+__global__ void __launch_bounds__(128) step_edge_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p,
+                                                        const int2 *__restrict__ list, int n)
+{
+    using R = typename Store<ST>::R;
+    __shared__ PopC<R> pc[2][LB_QMAX];
+    __shared__ MomC<R> mc[2][LB_QMAX];
+    stage_consts(p, pc, mc, threadIdx.x, 128);
+    __syncthreads();
+    const int k = blockIdx.x * 128 + threadIdx.x;
+    if (k >= n) return;
+    const int2 e = list[k];
+    const int x0 = e.x, j = e.y;
+    if (j < 0 || j >= p.ny || x0 < 0 || x0 >= p.nx) return;
+    const uint8_t flags = p.tmap[(size_t)j * p.ntx + x0 / LB_TILE_X];
+    if (flags & LB_TILE_IFACE) return;   /* mode A interface rows: set by iface_kernel */
+    const int s = flags & LB_TILE_HIGH;
+    const int q = p.set[s].q;
+    if (q == 9) step_cells<ST, 9>(p, s, flags, x0, j, pc[s], mc[s]);
+    else if (q == 16) step_cells<ST, 16>(p, s, flags, x0, j, pc[s], mc[s]);
+    else step_cells<ST, 36>(p, s, flags, x0, j, pc[s], mc[s]);
+}
+
+/* The edge kernel goes to edge_stream (the caller orders it after the previous step and
+ * before the next one): its few long-running blocks then overlap the plain kernel. */
+template <int ST>
+void launch_step_split_store(const StepParams<typename Store<ST>::R> &p, int rb, const int2 *edge, int n_edge,
+                             void *stream, void *edge_stream)
+{
+    const dim3 grid((p.nx + 4 * 32 - 1) / (4 * 32), (p.ny + 7) / 8);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n_edge > 0)
+        step_edge_kernel<ST><<<(n_edge + 127) / 128, 128, 0, static_cast<cudaStream_t>(edge_stream)>>>(p, edge, n_edge);
+    if (rb == 2) {
+        if (p.has_force) step_plain_kernel<ST, 2, true><<<grid, dim3(32, 4), 0, st>>>(p);
+        else step_plain_kernel<ST, 2, false><<<grid, dim3(32, 4), 0, st>>>(p);
+    } else {
+        if (p.has_force) step_plain_kernel<ST, 1, true><<<grid, dim3(32, 8), 0, st>>>(p);
+        else step_plain_kernel<ST, 1, false><<<grid, dim3(32, 8), 0, st>>>(p);
+    }
+}
 
 template <int ST>
 void launch_step_store(const StepParams<typename Store<ST>::R> &p, void *stream)

@@ -4,4 +4,5 @@
 
 namespace lbk {
 template void launch_step_store<3>(const StepParams<typename Store<3>::R> &, void *);
+template void launch_step_split_store<3>(const StepParams<typename Store<3>::R> &, int, const int2 *, int, void *, void *);
 }

@@ -132,10 +132,13 @@ def test_oscillating_wall_fp64():
     assert max(errs.values()) < F64_TOL, errs
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+LAYOUTS = [0, 1, 2, 3]
+
+
+@pytest.mark.parametrize("variant", LAYOUTS)
 def test_every_kernel_layout_matches_oracle(variant):
     """The step-kernel layouts the autotuner chooses from (one node quad per thread,
-    TMA-fed tiles) both reproduce the oracle."""
+    TMA-fed tiles, 4 x 2 and 4 x 4 register blocks) all reproduce the oracle."""
     w = ragged_workload()
     for store, tol in (("f64", F64_TOL), ("f32_dev", 1e-6), ("f32", 1e-4)):
         if store == "f64" and variant == 1:
@@ -222,14 +225,29 @@ def test_poiseuille_full_size_columns_match_oracle():
     assert err < F32_VEL_TOL, err
 
 
-@pytest.mark.parametrize("variant", [0, 1])
-def test_long_channel_tma_matches_one_row_layout(variant):
+@pytest.mark.parametrize("variant", LAYOUTS)
+def test_long_channel_every_layout_matches_oracle(variant):
     """Pressure channel with x-varying bands (several row-blocks, ragged last block,
-    x-interfaces): the TMA-fed layout against the oracle."""
+    x-interfaces, pressure columns): every layout against the oracle."""
     w = long_channel(nx=700, ny=45, steps=60)
     lat, o, eff, got, ref = run_both(w, "f32_dev", w.steps, variant=variant)
     errs = field_errors(got, ref)
     assert errs["u"] < F32_VEL_TOL and errs["rho"] < F32_VEL_TOL, errs
+
+
+@pytest.mark.parametrize("store", ["f64", "f32_dev", "bf16_dev"])
+@pytest.mark.parametrize("variant", [2, 3])
+def test_register_block_layouts_equal_quad_layout(store, variant):
+    """The register-block layouts do the quad layout's arithmetic in the same order, so
+    their populations agree with it bit for bit (walls, force, periodic edges, a ragged
+    tile and interface tiles fall back to the quad path inside the same launch)."""
+    w = ragged_workload()
+    a, _, _ = make_pair(w, store=store, variant=0)
+    b, _, _ = make_pair(ragged_workload(), store=store, variant=variant)
+    a.step(40)
+    b.step(40)
+    for s in (0, 1):
+        assert np.array_equal(a.populations(s), b.populations(s)), (store, variant, s)
 
 
 def test_long_channel_full_size_fp32():
