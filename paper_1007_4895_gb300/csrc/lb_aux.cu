@@ -120,27 +120,46 @@ __global__ void moments_kernel(const __grid_constant__ StepParams<typename Store
 /* FP64 sums over every node: mass, |u - u_prev|^2, |u|^2, count of non-finite nodes.
  * Warp shuffles, then shared memory, then one partial per block; the last block to
  * finish adds the partials in block order (deterministic) and resets the counter. */
+template <int ST, int Q>
+__device__ __forceinline__ void node_moments(const typename Store<ST>::T *f, size_t plane,
+                                             const MomC<typename Store<ST>::R> *mc, typename Store<ST>::R rho0,
+                                             typename Store<ST>::R &rd, typename Store<ST>::R &jx,
+                                             typename Store<ST>::R &jy)
+{
+    using R = typename Store<ST>::R;
+    rd = jx = jy = R(0);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const R d = decode<ST>(f[a * plane], mc[a].winv, rho0);
+        rd = fma(mc[a].w, d, rd);
+        jx = fma(mc[a].wcx, d, jx);
+        jy = fma(mc[a].wcy, d, jy);
+    }
+}
+
 template <int ST>
-__global__ void reduce_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p,
-                              typename Store<ST>::R *uprev, double *part, unsigned int *counter, double *out)
+__global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p,
+                                                     typename Store<ST>::R *uprev, double *part, unsigned int *counter,
+                                                     double *out)
 {
     using T = typename Store<ST>::T;
     using R = typename Store<ST>::R;
+    __shared__ PopC<R> pcs[2][LB_QMAX];
+    __shared__ MomC<R> mcs[2][LB_QMAX];
+    stage_consts(p, pcs, mcs, threadIdx.x, blockDim.x);
+    __syncthreads();
     const size_t N = (size_t)p.nx * p.ny;
     const size_t plane = p.plane;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(n % p.nx), j = (int)(n / p.nx);
+        const int j = (int)(n / p.nx), x = (int)(n - (size_t)j * p.nx);
         const int s = p.tmap[(size_t)j * p.ntx + x / LB_TILE_X] & LB_TILE_HIGH;
-        const SetConst<R> &c = p.set[s];
         const T *f = static_cast<const T *>(p.fin[s]) + (size_t)j * p.pitch + x + LB_GHOST;
-        R rd = R(0), jx = R(0), jy = R(0);
-        for (int a = 0; a < c.q; ++a) {
-            const R d = decode<ST>(f[a * plane], c.winv[a], p.rho0);
-            rd = fma(c.w[a], d, rd);
-            jx = fma(c.wcx[a], d, jx);
-            jy = fma(c.wcy[a], d, jy);
-        }
+        R rd, jx, jy;
+        const int q = p.set[s].q;
+        if (q == 9) node_moments<ST, 9>(f, plane, mcs[s], p.rho0, rd, jx, jy);
+        else if (q == 16) node_moments<ST, 16>(f, plane, mcs[s], p.rho0, rd, jx, jy);
+        else node_moments<ST, 36>(f, plane, mcs[s], p.rho0, rd, jx, jy);
         const double rho = double(p.rho0) + double(rd);
         const double ux = double(jx) / rho, uy = double(jy) / rho;
         if (!isfinite(rho) || !isfinite(ux) || !isfinite(uy)) {
@@ -159,26 +178,39 @@ __global__ void reduce_kernel(const __grid_constant__ StepParams<typename Store<
     __shared__ double sh[32][4];
     __shared__ bool last;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int nw = (int)(blockDim.x / 32);
     if (lane == 0)
         for (int m = 0; m < 4; ++m) sh[warp][m] = acc[m];
     __syncthreads();
     if (threadIdx.x == 0) {
         double b[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int w = 0; w < (int)(blockDim.x / 32); ++w)
+        for (int w = 0; w < nw; ++w)
             for (int m = 0; m < 4; ++m) b[m] += sh[w][m];
         for (int m = 0; m < 4; ++m) part[4 * blockIdx.x + m] = b[m];
         __threadfence();
         last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        double t[4] = {0.0, 0.0, 0.0, 0.0};
-        for (unsigned b = 0; b < gridDim.x; ++b)
-            for (int m = 0; m < 4; ++m) t[m] += part[4 * b + m];
-        out[0] = t[0];
-        out[1] = t[2] > 0.0 ? sqrt(t[1] / t[2]) : 0.0;
-        out[2] = t[3];
+    if (!last) return;
+    /* last block: each thread adds the partials b = t, t + blockDim, ... in order, then
+     * a fixed warp and block tree (same order every call) */
+    __threadfence();
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+        for (int m = 0; m < 4; ++m) t[m] += __ldcg(&part[4 * b + m]);
+    for (int m = 0; m < 4; ++m)
+        for (int o = 16; o > 0; o >>= 1) t[m] += __shfl_down_sync(0xffffffffu, t[m], o);
+    __syncthreads();
+    if (lane == 0)
+        for (int m = 0; m < 4; ++m) sh[warp][m] = t[m];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < nw; ++w)
+            for (int m = 0; m < 4; ++m) u[m] += sh[w][m];
+        out[0] = u[0];
+        out[1] = u[2] > 0.0 ? sqrt(u[1] / u[2]) : 0.0;
+        out[2] = u[3];
         *counter = 0u;
     }
 }
@@ -350,11 +382,12 @@ template void launch_features<double>(const StepParams<double> &, const float *,
 template void launch_hermite_residual<float>(int, const StepParams<float> &, float *, void *);
 template void launch_hermite_residual<double>(int, const StepParams<double> &, float *, void *);
 
+/* One node per thread (at most 16384 blocks; larger lattices loop). */
 int reduce_blocks(int nx, int ny)
 {
     long long n = (long long)nx * ny;
     long long b = (n + 255) / 256;
-    if (b > 4 * 152) b = 4 * 152;
+    if (b > 16384) b = 16384;
     return (int)(b < 1 ? 1 : b);
 }
 
