@@ -266,6 +266,41 @@ int lb_learned_map_now(lb_ctx *ctx);
 /* Map updates run, fallbacks taken, and the share of nodes on high-order tiles. */
 int lb_map_stats(lb_ctx *ctx, int64_t *updates, int64_t *fallbacks, double *high_fraction);
 
+/* ---------------------------------------------------------------------------------
+ * Batched channels. Many small independent lattices (e.g. a sweep of channel heights,
+ * Knudsen numbers and wall speeds) advanced together by ONE persistent kernel launch
+ * per call instead of one launch per lattice and step. Each lattice is an ordinary
+ * context (lb_batch_instance gives it back for lb_moments, lb_get_populations, ...) and
+ * takes exactly the steps of lb_step: the batched kernel does the one-quad layout's
+ * arithmetic in the same order, so the results are the same bits.
+ * ------------------------------------------------------------------------------- */
+typedef struct lb_batch lb_batch;
+
+/* n lattices, lattice i described by grids[i], maps[i] (host [ny_i][nx_i]), kn[i],
+ * walls[4 i .. 4 i + 3] and opts[i] as for lb_create. All share `sets`, opts.store and
+ * opts.rho0; every lattice needs opts.iface = LB_IFACE_HERMITE, reduce_every = 0, walls
+ * without oscillation (omega = 0) and no pressure sides (else LB_ERR_INVALID, checked
+ * before any device work). The kernel runs on opts[0].stream; device memory comes from
+ * opts[0]'s allocator. Lattices start from rest (rho0, u = 0). lb_batch_create times
+ * block sizes 128 / 256 / 512 on the batch and keeps the fastest. */
+int lb_batch_create(int32_t n, const lb_grid *grids, const uint8_t *const *maps, const int32_t sets[2],
+                    const lb_kn *kn, const lb_wall *walls, const lb_opts *opts, lb_batch **out);
+/* Every lattice nsteps steps: one persistent launch. Asynchronous. */
+int lb_batch_step(lb_batch *b, int64_t nsteps);
+/* The same through lb_step on each lattice in turn, one step at a time (the
+ * one-launch-per-lattice path, for comparison). */
+int lb_batch_step_each(lb_batch *b, int64_t nsteps);
+/* Capture lb_batch_step(nsteps) (nsteps even) in a CUDA graph and replay it `replays`
+ * times; synchronous. */
+int lb_batch_graph(lb_batch *b, int64_t nsteps, int32_t replays);
+/* Lattice i (owned by the batch: do not destroy, do not step it alone). */
+lb_ctx *lb_batch_instance(lb_batch *b, int32_t i);
+/* Block size and persistent grid chosen by the timing at creation. */
+int lb_batch_info(lb_batch *b, int32_t *block_threads, int32_t *grid_blocks);
+/* Waits for the batch's stream; returns the first sticky lattice status. */
+int lb_batch_sync(lb_batch *b);
+void lb_batch_destroy(lb_batch *b);
+
 /* Mass / residual reduction that allocates no device memory (the paper has no
  * counterpart: this is for callers that cannot allocate, e.g. code running under a
  * memory budget fixed by its host application, code whose allocator belongs to another

@@ -33,7 +33,8 @@ EXPORTS = ("lb_create", "lb_init_equilibrium", "lb_step", "lb_moments", "lb_redu
            "lb_state_store", "lb_save", "lb_load", "lb_info", "lb_sync", "lb_destroy", "lb_last_error",
            "lb_reduce_fields_noalloc", "lb_features", "lb_hermite_residual", "lb_mlp_create", "lb_mlp_grad",
            "lb_mlp_adam_step", "lb_mlp_train", "lb_mlp_get_params", "lb_mlp_infer", "lb_mlp_destroy", "lb_set_mlp",
-           "lb_learned_map_now", "lb_map_stats")
+           "lb_learned_map_now", "lb_map_stats", "lb_batch_create", "lb_batch_step", "lb_batch_step_each",
+           "lb_batch_graph", "lb_batch_instance", "lb_batch_info", "lb_batch_sync", "lb_batch_destroy")
 LB_NOALLOC_MAX_NODES = 524288
 
 
@@ -112,6 +113,17 @@ def _load():
     L.lb_set_mlp.argtypes = [P, P, ctypes.c_int32, ctypes.c_float, ctypes.c_float]
     L.lb_learned_map_now.argtypes = [P]
     L.lb_map_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), dp]
+    L.lb_batch_create.argtypes = [ctypes.c_int32, ctypes.POINTER(lb_grid), ctypes.POINTER(P), ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(lb_kn), ctypes.POINTER(lb_wall), ctypes.POINTER(lb_opts), ctypes.POINTER(P)]
+    L.lb_batch_step.argtypes = [P, ctypes.c_int64]
+    L.lb_batch_step_each.argtypes = [P, ctypes.c_int64]
+    L.lb_batch_graph.argtypes = [P, ctypes.c_int64, ctypes.c_int32]
+    L.lb_batch_instance.argtypes = [P, ctypes.c_int32]
+    L.lb_batch_instance.restype = P
+    L.lb_batch_info.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.lb_batch_sync.argtypes = [P]
+    L.lb_batch_destroy.argtypes = [P]
+    L.lb_batch_destroy.restype = None
     return L
 
 
@@ -383,8 +395,20 @@ class Lattice:
 
     def close(self):
         if getattr(self, "ctx", None):
-            lb_destroy(self.ctx)
+            if getattr(self, "_owned", True):
+                lb_destroy(self.ctx)
             self.ctx = None
+
+    @classmethod
+    def _view(cls, ctx, nx, ny, sets, store, owner):
+        """A lattice owned by something else (a batch): used like any lattice, never
+        destroyed through this object."""
+        lat = cls.__new__(cls)
+        lat.nx, lat.ny, lat.sets, lat.store = int(nx), int(ny), tuple(sets), store
+        lat.ctx, lat._owned, lat._owner, lat._alloc = ctx, False, owner, None
+        info = lb_info(ctx)
+        lat.dt, lat.h = info["dt"], info["h"]
+        return lat
 
     def __del__(self):
         try:
@@ -463,3 +487,92 @@ class Lattice:
 
     def sync(self):
         return lb_sync(self.ctx)
+
+
+# ----------------------------------------------------------------- Batch
+
+class Batch:
+    """Many small lattices advanced together by one persistent kernel launch per call
+    (include/lb.h, lb_batch_*). `workloads` are lbinputs.Workload objects sharing the
+    velocity sets; a workload's `init` (rho, ux, uy) is applied to its lattice."""
+
+    def __init__(self, workloads, store="f32", stream=None, torch_allocator=True):
+        import torch
+        stream = stream or torch.cuda.current_stream()
+        self._alloc = _TorchAllocator(stream) if torch_allocator else None
+        sp = getattr(stream, "cuda_stream", stream)
+        ws = list(workloads)
+        n = len(ws)
+        self.store = STORES[store] if isinstance(store, str) else int(store)
+        self.sets = tuple(int(x) for x in ws[0].sets)
+        grids, kns = (lb_grid * n)(), (lb_kn * n)()
+        walls, opts = (lb_wall * (4 * n))(), (lb_opts * n)()
+        maps = [np.ascontiguousarray(np.asarray(w.region_map, dtype=np.uint8).reshape(w.ny, w.nx)) for w in ws]
+        mp = (ctypes.c_void_p * n)(*[m.ctypes.data for m in maps])
+        for i, w in enumerate(ws):
+            if tuple(int(x) for x in w.sets) != self.sets:
+                raise ValueError("batched lattices share the velocity sets")
+            grids[i] = lb_grid(w.nx, w.ny, 0.0, w.cfl, 0.0)
+            kns[i] = lb_kn(w.kn_ref, w.rho_ref, w.tau_mode)
+            for k, wl in enumerate(_walls(w.walls)):
+                walls[4 * i + k] = wl
+            o = opts[i]
+            o.store = self.store
+            o.iface = LB_IFACE_HERMITE if w.iface == "hermite" else LB_IFACE_PAPER
+            o.rho0, o.gx, o.gy = w.rho0, w.gx, w.gy
+            o.reduce_every, o.variant, o.stream = 0, 0, sp
+            if self._alloc:
+                o.alloc, o.free = self._alloc.alloc, self._alloc.free
+        self._keep = (grids, kns, walls, opts, maps, mp)
+        self.ptr = ctypes.c_void_p()
+        _check(_lib.lb_batch_create(n, grids, mp, (ctypes.c_int32 * 2)(*self.sets), kns, walls, opts,
+                                    ctypes.byref(self.ptr)))
+        self.n, self.workloads = n, ws
+        self._views = [None] * n
+        for i, w in enumerate(ws):
+            if w.init is not None:
+                self.lattice(i).init_equilibrium(*w.init)
+
+    def step(self, n=1):
+        _check(_lib.lb_batch_step(self.ptr, int(n)))
+
+    def step_each(self, n=1):
+        _check(_lib.lb_batch_step_each(self.ptr, int(n)))
+
+    def graph(self, nsteps, replays=1):
+        _check(_lib.lb_batch_graph(self.ptr, int(nsteps), int(replays)))
+
+    def sync(self):
+        _check(_lib.lb_batch_sync(self.ptr))
+
+    def info(self):
+        t, g = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.lb_batch_info(self.ptr, ctypes.byref(t), ctypes.byref(g)))
+        return {"block_threads": t.value, "grid_blocks": g.value}
+
+    def lattice(self, i):
+        if self._views[i] is None:
+            ctx = _lib.lb_batch_instance(self.ptr, int(i))
+            if not ctx:
+                raise LBError(LB_ERR_INVALID, _lib.lb_last_error().decode())
+            w = self.workloads[i]
+            self._views[i] = Lattice._view(ctypes.c_void_p(ctx), w.nx, w.ny, self.sets, self.store, self)
+        return self._views[i]
+
+    @property
+    def cells(self):
+        return sum(w.nx * w.ny for w in self.workloads)
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            for v in self._views:
+                if v is not None:
+                    v.ctx = None
+            _lib.lb_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1165,6 +1165,314 @@ int lb_map_stats(lb_ctx *c, int64_t *updates, int64_t *fallbacks, double *high_f
     return LB_OK;
 }
 
+}  // extern "C"
+
+/* ---------------------------------------------------------------- batches -- */
+
+struct lb_batch {
+    std::vector<lb_ctx *> inst;
+    int n = 0, store = 0;
+    lb_opts opts{};
+    cudaStream_t stream = nullptr, cstream = nullptr;
+    void *d_params = nullptr;       /* StepParams [n][2] of the storage's arithmetic type */
+    int *d_order = nullptr;         /* queue order: most work first */
+    unsigned int *d_queue = nullptr;
+    int threads = 256, grid = 1;
+    int phase = 0;                  /* lattices' current level, relative to params [i][0] */
+    int status = LB_OK;
+    std::vector<void *> owned;
+};
+
+namespace {
+
+void *batch_alloc(lb_batch *b, size_t bytes)
+{
+    void *p = nullptr;
+    if (b->opts.alloc && b->opts.free) {
+        p = b->opts.alloc(bytes, b->opts.alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) b->owned.push_back(p);
+    return p;
+}
+
+void batch_release(lb_batch *b)
+{
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (lb_ctx *c : b->inst) lb_destroy(c);
+    b->inst.clear();
+    for (void *p : b->owned) {
+        if (b->opts.alloc && b->opts.free) b->opts.free(p, b->opts.alloc_user);
+        else cudaFree(p);
+    }
+    b->owned.clear();
+    if (b->cstream) cudaStreamDestroy(b->cstream);
+    b->cstream = nullptr;
+}
+
+template <typename R>
+int batch_upload_params(lb_batch *b)
+{
+    std::vector<StepParams<R>> h(2 * (size_t)b->n);
+    for (int i = 0; i < b->n; ++i) {
+        const lb_ctx *c = b->inst[i];
+        h[2 * (size_t)i] = make_params<R>(c, c->cur, c->cur ^ 1, c->t + c->dt);
+        h[2 * (size_t)i + 1] = make_params<R>(c, c->cur ^ 1, c->cur, c->t + 2.0 * c->dt);
+    }
+    b->d_params = batch_alloc(b, h.size() * sizeof(StepParams<R>));
+    if (!b->d_params) return fail(LB_ERR_NOMEM, "device allocation failed");
+    if (cudaMemcpyAsync(b->d_params, h.data(), h.size() * sizeof(StepParams<R>), cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return fail(LB_ERR_CUDA, "batch parameter upload failed");
+    return LB_OK;
+}
+
+int batch_launch(lb_batch *b, int64_t nsteps, int advance, cudaStream_t st)
+{
+    if (cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned int), st) != cudaSuccess)
+        return fail(LB_ERR_CUDA, "batch queue reset failed");
+    if (lbk::launch_batch(b->store, b->d_params, b->d_order, b->n, (int)nsteps, b->phase, advance, b->d_queue, b->threads,
+                          b->grid, st) != 0)
+        return fail(LB_ERR_INVALID, "bad batch block shape");
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        b->status = LB_ERR_CUDA;
+        return fail(LB_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    }
+    return LB_OK;
+}
+
+/* after nsteps steps of every lattice */
+void batch_advance(lb_batch *b, int64_t nsteps)
+{
+    for (lb_ctx *c : b->inst) {
+        c->cur ^= (int)(nsteps & 1);
+        c->t += (double)nsteps * c->dt;
+        c->step += nsteps;
+    }
+    b->phase ^= (int)(nsteps & 1);
+}
+
+int batch_ready(lb_batch *b)
+{
+    if (!b) return fail(LB_ERR_INVALID, "null batch");
+    if (b->status != LB_OK) return b->status;
+    for (lb_ctx *c : b->inst) {
+        if (c->status != LB_OK) return c->status;
+        if (c->cur != b->phase) return fail(LB_ERR_INVALID, "a lattice of the batch was stepped on its own");
+    }
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_batch_create(int32_t n, const lb_grid *grids, const uint8_t *const *maps, const int32_t sets[2], const lb_kn *kn,
+                    const lb_wall *walls, const lb_opts *opts, lb_batch **out)
+{
+    g_err.clear();
+    if (!out) return fail(LB_ERR_INVALID, "null output");
+    *out = nullptr;
+    if (n < 1 || !grids || !maps || !sets || !kn || !walls || !opts) return fail(LB_ERR_INVALID, "null argument or n < 1");
+    for (int i = 0; i < n; ++i) {
+        const lb_opts &o = opts[i];
+        if (!maps[i]) return fail(LB_ERR_INVALID, "null region map");
+        if (o.iface != LB_IFACE_HERMITE) return fail(LB_ERR_INVALID, "batched lattices need LB_IFACE_HERMITE");
+        if (o.reduce_every != 0) return fail(LB_ERR_INVALID, "batched lattices take no in-step reductions");
+        if (o.store != opts[0].store || o.rho0 != opts[0].rho0)
+            return fail(LB_ERR_INVALID, "batched lattices share the storage format and rho0");
+        for (int k = 0; k < 4; ++k) {
+            const lb_wall &wl = walls[4 * (size_t)i + k];
+            if (wl.kind == LB_WALL_PRESSURE) return fail(LB_ERR_INVALID, "batched lattices have no pressure sides");
+            if (wl.omega != 0.0) return fail(LB_ERR_INVALID, "batched lattices have steady walls");
+        }
+    }
+    lb_batch *b = new lb_batch();
+    b->n = n;
+    b->opts = opts[0];
+    b->store = opts[0].store;
+    b->stream = static_cast<cudaStream_t>(opts[0].stream);
+    for (int i = 0; i < n; ++i) {
+        lb_opts o = opts[i];
+        o.variant = 0;   /* no per-lattice timing: the batch kernel does the stepping */
+        o.stream = opts[0].stream;
+        lb_ctx *c = nullptr;
+        if (int e = lb_create(&grids[i], maps[i], sets, &kn[i], walls + 4 * (size_t)i, &o, &c)) {
+            const std::string msg = "lattice " + std::to_string(i) + ": " + g_err;
+            batch_release(b);
+            delete b;
+            return fail(e, msg);
+        }
+        b->inst.push_back(c);
+    }
+    /* most work first */
+    std::vector<std::pair<double, int>> work(n);
+    for (int i = 0; i < n; ++i) {
+        const lb_ctx *c = b->inst[i];
+        double w = 0.0;
+        for (int j = 0; j < c->ny; ++j)
+            for (int tx = 0; tx < c->ntx; ++tx) {
+                const int cols = std::min(c->nx, (tx + 1) * LB_TILE_X) - tx * LB_TILE_X;
+                w += (double)cols * c->q[c->tmap[(size_t)j * c->ntx + tx] & LB_TILE_HIGH];
+            }
+        work[i] = {-w, i};
+    }
+    std::sort(work.begin(), work.end());
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = work[i].second;
+    b->d_order = static_cast<int *>(batch_alloc(b, sizeof(int) * n));
+    b->d_queue = static_cast<unsigned int *>(batch_alloc(b, 256));
+    int e = (b->d_order && b->d_queue) ? LB_OK : fail(LB_ERR_NOMEM, "device allocation failed");
+    if (!e && cudaMemcpyAsync(b->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+        e = fail(LB_ERR_CUDA, "batch order upload failed");
+    if (!e) e = b->store == LB_STORE_F64 ? batch_upload_params<double>(b) : batch_upload_params<float>(b);
+    /* block size: time each candidate on the batch without moving the state */
+    int dev = 0, nsm = 0;
+    if (!e && (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess))
+        e = fail(LB_ERR_CUDA, "device query failed");
+    if (!e) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        int best_threads = 0, best_grid = 0;
+        for (int threads : {128, 256, 512}) {
+            const int per_sm = lbk::batch_blocks(b->store, threads);
+            if (per_sm < 1) continue;
+            b->threads = threads;
+            b->grid = std::min(n, nsm * per_sm);
+            float ms = 1e30f;
+            for (int rep = 0; rep < 2 && !e; ++rep) {
+                cudaEventRecord(e0, b->stream);
+                e = batch_launch(b, 4, 0, b->stream);
+                cudaEventRecord(e1, b->stream);
+                float t = 0.0f;
+                if (!e && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
+                    ms = std::min(ms, t);
+            }
+            if (!e && ms < best) {
+                best = ms;
+                best_threads = b->threads;
+                best_grid = b->grid;
+            }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (!e && best_threads > 0) {
+            b->threads = best_threads;
+            b->grid = best_grid;
+        } else if (!e) {
+            e = fail(LB_ERR_CUDA, "no batch block size could be launched");
+        }
+    }
+    if (e) {
+        batch_release(b);
+        delete b;
+        return e;
+    }
+    *out = b;
+    return LB_OK;
+}
+
+int lb_batch_step(lb_batch *b, int64_t nsteps)
+{
+    if (int e = batch_ready(b)) return e;
+    if (nsteps < 0 || nsteps > (1LL << 30)) return fail(LB_ERR_INVALID, "step count out of range");
+    if (nsteps == 0) return LB_OK;
+    if (int e = batch_launch(b, nsteps, 1, b->stream)) return e;
+    batch_advance(b, nsteps);
+    return LB_OK;
+}
+
+int lb_batch_step_each(lb_batch *b, int64_t nsteps)
+{
+    if (int e = batch_ready(b)) return e;
+    if (nsteps < 0) return fail(LB_ERR_INVALID, "negative step count");
+    for (int64_t k = 0; k < nsteps; ++k)
+        for (lb_ctx *c : b->inst)
+            if (int e = lb_step(c, 1)) return e;
+    b->phase ^= (int)(nsteps & 1);
+    return LB_OK;
+}
+
+int lb_batch_graph(lb_batch *b, int64_t nsteps, int32_t replays)
+{
+    if (int e = batch_ready(b)) return e;
+    if (nsteps < 2 || (nsteps & 1) || nsteps > (1LL << 30) || replays < 1)
+        return fail(LB_ERR_INVALID, "graph replays need an even step count >= 2 and replays >= 1");
+    if (!b->cstream && cudaStreamCreateWithFlags(&b->cstream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        b->cstream = nullptr;
+        return fail(LB_ERR_CUDA, "capture stream creation failed");
+    }
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(LB_ERR_CUDA, "batch stream sync failed");
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    if (cudaStreamBeginCapture(b->cstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LB_ERR_CUDA, "stream capture failed to start");
+    }
+    const int el = batch_launch(b, nsteps, 1, b->cstream);
+    const cudaError_t ec = cudaStreamEndCapture(b->cstream, &g);
+    if (el || ec != cudaSuccess || !g) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        return el ? el : fail(LB_ERR_CUDA, "stream capture failed");
+    }
+    cudaError_t ce = cudaGraphInstantiate(&x, g, 0);
+    for (int r = 0; r < replays && ce == cudaSuccess; ++r) ce = cudaGraphLaunch(x, b->cstream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->cstream);
+    if (x) cudaGraphExecDestroy(x);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+        b->status = LB_ERR_CUDA;
+        return fail(LB_ERR_CUDA, std::string("graph replay: ") + cudaGetErrorString(ce));
+    }
+    batch_advance(b, nsteps * (int64_t)replays);
+    return LB_OK;
+}
+
+lb_ctx *lb_batch_instance(lb_batch *b, int32_t i)
+{
+    if (!b || i < 0 || i >= b->n) {
+        fail(LB_ERR_INVALID, "no such lattice in the batch");
+        return nullptr;
+    }
+    return b->inst[i];
+}
+
+int lb_batch_info(lb_batch *b, int32_t *block_threads, int32_t *grid_blocks)
+{
+    if (!b) return fail(LB_ERR_INVALID, "null batch");
+    if (block_threads) *block_threads = b->threads;
+    if (grid_blocks) *grid_blocks = b->grid;
+    return LB_OK;
+}
+
+int lb_batch_sync(lb_batch *b)
+{
+    if (!b) return fail(LB_ERR_INVALID, "null batch");
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        b->status = LB_ERR_CUDA;
+        return fail(LB_ERR_CUDA, "batch stream sync failed");
+    }
+    if (b->status != LB_OK) return b->status;
+    for (lb_ctx *c : b->inst)
+        if (c->status != LB_OK) return c->status;
+    return LB_OK;
+}
+
+void lb_batch_destroy(lb_batch *b)
+{
+    if (!b) return;
+    batch_release(b);
+    delete b;
+}
+
 int lb_info(lb_ctx *c, double *dt, double *h, int64_t *step, double *time, int32_t *variant)
 {
     if (!c) return fail(LB_ERR_INVALID, "null context");

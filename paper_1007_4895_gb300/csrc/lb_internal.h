@@ -89,6 +89,15 @@ void launch_step(int store, const StepParams<R> &p, void *stream);
 template <typename R>
 void launch_step_split(int store, const StepParams<R> &p, int rb, const int2 *edge, int n_edge, void *stream,
                        void *edge_stream);
+/* Batched lattices, one persistent launch: params [n][2] launch parameter sets
+ * (StepParams of the storage's arithmetic type; [i][0] reads level cur, [i][1] the
+ * other level), order [n] the queue order, base the parity of level cur relative to
+ * [i][0]; advance = 0 repeats the first step without moving the state. Returns 0 or -1
+ * for a bad shape. */
+int launch_batch(int store, const void *params, const int *order, int n, int nsteps, int base, int advance,
+                 unsigned int *queue, int threads, int grid, void *stream);
+/* resident blocks per SM of the batch kernel for a block size (0 on error) */
+int batch_blocks(int store, int threads);
 /* step-kernel layouts: 0 one node quad per thread, 1 TMA-fed producer / consumer,
  * 2 and 3 split plain / edge kernels with register blocks of 4 x 1 and 4 x 2 nodes */
 #define LB_NUM_VARIANTS 4

@@ -215,6 +215,27 @@ void launch_step(int store, const StepParams<R> &p, void *stream)
     LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) launch_step_store<ST>(p, stream));
 }
 
+template <int ST>
+int launch_batch_store(const void *params, const int *order, int n, int nsteps, int base, int advance,
+                       unsigned int *queue, int threads, int grid, void *stream);
+template <int ST>
+int batch_blocks_per_sm(int threads);
+
+int launch_batch(int store, const void *params, const int *order, int n, int nsteps, int base, int advance,
+                 unsigned int *queue, int threads, int grid, void *stream)
+{
+    int r = -1;
+    LB_DISPATCH(store, r = launch_batch_store<ST>(params, order, n, nsteps, base, advance, queue, threads, grid, stream));
+    return r;
+}
+
+int batch_blocks(int store, int threads)
+{
+    int r = 0;
+    LB_DISPATCH(store, r = batch_blocks_per_sm<ST>(threads));
+    return r;
+}
+
 template <typename R>
 void launch_step_split(int store, const StepParams<R> &p, int rb, const int2 *edge, int n_edge, void *stream,
                        void *edge_stream)

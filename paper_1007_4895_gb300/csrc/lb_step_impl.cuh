@@ -688,6 +688,86 @@ void launch_step_split_store(const StepParams<typename Store<ST>::R> &p, int rb,
     }
 }
 
+/* ------------------------------------------------------------------------------
+ * Batched channels: many independent lattices advanced by one persistent launch. Each
+ * block takes lattices from a queue (longest first), copies the lattice's two launch
+ * parameter sets (level n -> n+1 and back) into shared memory and advances it nsteps
+ * steps, a block barrier between steps (the block owns the whole lattice, so no other
+ * synchronisation is needed). Every quad goes through step_cells: the same arithmetic,
+ * in the same order, as the one-quad layout of a single lattice. The lattices have
+ * mode-B interfaces, steady walls and no pressure columns (checked on the host).
+ * advance = 0 repeats step 0 (level n -> n+1) nsteps times without moving the state
+ * (used to time block shapes).
+ * ---------------------------------------------------------------------------- */
+template <int ST>
+__global__ void __launch_bounds__(512) batch_kernel(const StepParams<typename Store<ST>::R> *__restrict__ params,
+                                                   const int *__restrict__ order, int n, int nsteps, int base,
+                                                   int advance, unsigned int *queue)
+{
+    using R = typename Store<ST>::R;
+    __shared__ StepParams<R> sp[2];
+    __shared__ PopC<R> pc[2][LB_QMAX];
+    __shared__ MomC<R> mc[2][LB_QMAX];
+    __shared__ int inst_sh;
+    static_assert(sizeof(StepParams<R>) % 4 == 0, "parameter copy in 4-byte words");
+    constexpr int NW = (int)(sizeof(StepParams<R>) / 4);
+    for (;;) {
+        __syncthreads();   /* every thread is done with the previous lattice */
+        if (threadIdx.x == 0) {
+            const unsigned k = atomicAdd(queue, 1u);
+            inst_sh = k < (unsigned)n ? order[k] : -1;
+        }
+        __syncthreads();
+        const int inst = inst_sh;
+        if (inst < 0) return;
+        {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(params + 2 * (size_t)inst);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(sp);
+            for (int k = threadIdx.x; k < 2 * NW; k += blockDim.x) dst[k] = src[k];
+        }
+        __syncthreads();
+        stage_consts(sp[0], pc, mc, threadIdx.x, blockDim.x);
+        __syncthreads();
+        const int nqx = (sp[0].nx + 3) / 4, nq = nqx * sp[0].ny;
+        for (int st = 0; st < nsteps; ++st) {
+            const StepParams<R> &p = sp[advance ? ((base + st) & 1) : base];
+            for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+                const int j = k / nqx, x0 = (k - j * nqx) * 4;
+                const uint8_t flags = p.tmap[(size_t)j * p.ntx + x0 / LB_TILE_X];
+                const int s = flags & LB_TILE_HIGH;
+                const int q = p.set[s].q;
+                if (q == 9) step_cells<ST, 9>(p, s, flags, x0, j, pc[s], mc[s]);
+                else if (q == 16) step_cells<ST, 16>(p, s, flags, x0, j, pc[s], mc[s]);
+                else step_cells<ST, 36>(p, s, flags, x0, j, pc[s], mc[s]);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <int ST>
+int launch_batch_store(const void *params, const int *order, int n, int nsteps, int base, int advance,
+                       unsigned int *queue, int threads, int grid, void *stream)
+{
+    using R = typename Store<ST>::R;
+    if (threads < 32 || threads > 512 || grid < 1) return -1;
+    batch_kernel<ST><<<grid, threads, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const StepParams<R> *>(params), order, n, nsteps, base, advance, queue);
+    return 0;
+}
+
+/* Resident blocks per SM of the batch kernel at this block size. */
+template <int ST>
+int batch_blocks_per_sm(int threads)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<ST>, threads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm;
+}
+
 template <int ST>
 void launch_step_store(const StepParams<typename Store<ST>::R> &p, void *stream)
 {

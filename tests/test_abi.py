@@ -84,3 +84,57 @@ def test_paper_interface_mode_needs_x_uniform_rows(lb):
     with pytest.raises(lb.LBError) as e:
         lb.lb_create(grid, m, sets, kn, walls, opts)
     assert e.value.code == lb.LB_ERR_INVALID
+
+
+def _batch_call(lb, n=2, **over):
+    """lb_batch_create with n small lattices; `over` changes lattice 1."""
+    grids = (lb.lb_grid * n)(*[lb.lb_grid(8, 16, 0.0, 0.5, 0.0) for _ in range(n)])
+    kns = (lb.lb_kn * n)(*[lb.lb_kn(0.1, 1.0, 0) for _ in range(n)])
+    walls = (lb.lb_wall * (4 * n))()
+    for i in range(n):
+        walls[4 * i + 0] = lb.lb_wall(1, 0.0, 0.0, 1.0, 0.0)
+        walls[4 * i + 1] = lb.lb_wall(1, 0.05, 0.0, 1.0, 0.0)
+        walls[4 * i + 2] = lb.lb_wall(0, 0.0, 0.0, 1.0, 0.0)
+        walls[4 * i + 3] = lb.lb_wall(0, 0.0, 0.0, 1.0, 0.0)
+    opts = (lb.lb_opts * n)()
+    for i in range(n):
+        opts[i].store, opts[i].iface, opts[i].rho0 = 1, 1, 1.0
+    for k, v in over.get("walls", {}).items():
+        walls[4 + k] = v
+    for k, v in over.get("opts", {}).items():
+        setattr(opts[1], k, v)
+    maps = [np.zeros((16, 8), np.uint8) for _ in range(n)]
+    mp = (ctypes.c_void_p * n)(*[m.ctypes.data for m in maps])
+    out = ctypes.c_void_p()
+    code = lb._lib.lb_batch_create(n, grids, mp, (ctypes.c_int32 * 2)(9, 36), kns, walls, opts, ctypes.byref(out))
+    return code, out
+
+
+@pytest.mark.parametrize("case", [
+    dict(opts={"iface": 0}),                        # mode A interface rows need their own pass
+    dict(opts={"reduce_every": 10}),                # no in-step reductions inside the batch
+    dict(opts={"store": 2}),                        # one storage format for the batch
+    dict(opts={"rho0": 2.0}),                       # one rest density for the batch
+    dict(walls={1: "osc"}),                         # oscillating wall
+    dict(walls={2: "pressure"}),                    # pressure side
+])
+def test_batch_restrictions_rejected_before_device_work(lb, case):
+    over = dict(case)
+    if "walls" in over:
+        k, kind = next(iter(over["walls"].items()))
+        if kind == "osc":
+            w = lb.lb_wall(1, 0.05, 0.0, 1.0, 2.0)
+            over["walls"] = {k: w}
+        else:
+            over["walls"] = {2: lb.lb_wall(2, 0.0, 0.0, 1.5, 0.0), 3: lb.lb_wall(2, 0.0, 0.0, 1.0, 0.0)}
+    code, out = _batch_call(lb, **over)
+    assert code == lb.LB_ERR_INVALID
+    assert not out.value
+    assert lb.lb_last_error()
+
+
+def test_batch_argument_checks(lb):
+    out = ctypes.c_void_p()
+    assert lb._lib.lb_batch_create(0, None, None, None, None, None, None, ctypes.byref(out)) == lb.LB_ERR_INVALID
+    assert lb._lib.lb_batch_step(None, 1) == lb.LB_ERR_INVALID
+    assert lb._lib.lb_batch_instance(None, 0) is None
