@@ -164,6 +164,24 @@ def batched_instances(n=512, seed=1007, nx=8, ny_range=(16, 256), kn_log_range=(
     return out
 
 
+def placement_channel(kn: float, region_map=None, nx=8, ny=64, u_lat=0.05, cfl=0.38) -> Workload:
+    """Steady force-driven channel of the learned-placement study: periodic x, resting
+    diffuse walls, the body force of a no-slip parabola with peak lattice speed u_lat,
+    CFL 0.38 so that an all-high-order map is stable; region_map defaults to all
+    high-order (the judge)."""
+    g = 8.0 * kn * lattice_speed(u_lat)
+    w = poiseuille(nx=nx, ny=ny, rows=1, kn=kn, g_lat=g / (3.0 * (ny - 1)))
+    w.region_map = np.ones((ny, nx), np.uint8) if region_map is None else np.asarray(region_map, np.uint8)
+    w.cfl = cfl
+    w.name = f"placement_{nx}x{ny}_kn{kn:g}"
+    return w
+
+
+def steady_steps(kn: float, dt: float) -> int:
+    """Steps to two viscous times H^2 / nu (nu ~ Kn) of the placement channel."""
+    return int(min(60000, max(4000, 2.0 / (kn * dt))))
+
+
 def config1() -> Workload:
     return couette(nx=4, ny=32, rows=4, kn=0.1, u_wall_lat=0.05, steps=5000)
 
