@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lb_api.cu", "lb_step.cu", "lb_step_st_f64.cu", "lb_step_st_f32.cu", "lb_step_st_f32dev.cu",
-           "lb_step_st_f16.cu", "lb_step_st_bf16.cu", "lb_step3.cu", "lb_aux.cu", "lb_mlp.cu", "lb_noalloc.cu", "quadrature.cpp"]
+           "lb_step_st_f16.cu", "lb_step_st_bf16.cu", "lb_step3.cu", "lb_stream.cu", "lb_aux.cu", "lb_mlp.cu", "lb_noalloc.cu", "quadrature.cpp"]
 
 
 def nvcc() -> str:

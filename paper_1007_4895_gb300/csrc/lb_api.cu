@@ -92,6 +92,13 @@ struct lb_ctx {
     int2 *d_edge[2] = {nullptr, nullptr};
     size_t edge_cap[2] = {0, 0};
     cudaStream_t edge_stream = nullptr;   /* the edge kernel runs here, overlapping */
+    /* streamed layout: carried moments per level, wall sums, quads whose carried
+     * moments are recomputed after the boundary post-passes */
+    void *aux[2] = {nullptr, nullptr};
+    void *wall_num = nullptr;
+    std::vector<int2> auxfix_h;
+    int2 *d_auxfix = nullptr;
+    size_t auxfix_cap = 0;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     /* learned placement */
     lb_mlp *mlp = nullptr;
@@ -187,6 +194,9 @@ StepParams<R> make_params(const lb_ctx *c, int in, int out, double t_new)
         p.fout[s] = static_cast<char *>(c->planes[out][s]) + row0;
     }
     p.plane = (size_t)(c->ny + 2 * LB_GHOST_ROWS) * c->pitch;
+    p.aux_in = c->aux[in];
+    p.aux_out = c->aux[out];
+    p.wall_num = c->wall_num;
     p.rho0 = R(c->opts.rho0);
     p.dt = R(c->dt);
     p.tau_const = c->kn.rho_ref > 0.0 ? 0 : 1;
@@ -311,6 +321,7 @@ int finalize_level_t(lb_ctx *c, int level)
     if (c->opts.iface == LB_IFACE_HERMITE) lbk::launch_shadows<R>(c->store, p, st);
     lbk::launch_iface<R>(c->store, p, st);
     lbk::launch_pressure<R>(c->store, p, st);
+    lbk::launch_aux<R>(c->store, p, nullptr, 0, st);   /* carried moments of this level */
     return launch_check(c, "finalize");
 }
 
@@ -357,6 +368,27 @@ int build_edge_lists(lb_ctx *c)
                                                   c->stream), "edge list upload"))
             return e;
     }
+    /* quads rewritten after the streamed kernel: diffuse-wall rows, pressure columns */
+    std::vector<int2> &A = c->auxfix_h;
+    A.clear();
+    for (int j = 0; j < c->ny; ++j) {
+        const bool wall_row = (j == 0 && c->walls[0].kind == LB_WALL_DIFFUSE) ||
+                              (j == c->ny - 1 && c->walls[1].kind == LB_WALL_DIFFUSE);
+        for (int x0 = 0; x0 < c->nx; x0 += 4)
+            if (wall_row || (pl && x0 == 0) || (ph && x0 + 3 >= c->nx - 1)) A.push_back(make_int2(x0, j));
+    }
+    if (!A.empty()) {
+        if (A.size() > c->auxfix_cap) {
+            const size_t cap = std::max(A.size(), 2 * c->auxfix_cap);
+            int2 *d = static_cast<int2 *>(own(c, cap * sizeof(int2)));
+            if (!d) return fail(LB_ERR_NOMEM, "device allocation failed");
+            c->d_auxfix = d;
+            c->auxfix_cap = cap;
+        }
+        if (int e = cuda_check(c, cudaMemcpyAsync(c->d_auxfix, A.data(), A.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                                  c->stream), "fix-up list upload"))
+            return e;
+    }
     return LB_OK;
 }
 
@@ -378,6 +410,14 @@ void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
     if constexpr (std::is_same<R, float>::value) {
         if (variant == 1 && c->tma_ok && lbk::launch_step3(c->store, p, c->maps[c->cur], c->d_err, c->stream) == 0)
             return;
+    }
+    if constexpr (std::is_same<R, float>::value) {
+        if (variant == 4 && c->tma_ok && lbk::launch_stream(c->store, p, c->maps[c->cur], c->d_err, c->stream) == 0) {
+            lbk::launch_wall_post<R>(c->store, p, c->stream);
+            lbk::launch_images<R>(c->store, p, c->stream);
+            if (c->opts.iface == LB_IFACE_HERMITE) lbk::launch_shadows<R>(c->store, p, c->stream);
+            return;
+        }
     }
     if (variant == 2 || variant == 3) {
         const int v = variant - 2;
@@ -401,6 +441,7 @@ bool variant_available(const lb_ctx *c, int v)
 {
     if (v == 1) return c->tma_ok;
     if (v == 2 || v == 3) return c->edge_stream != nullptr;
+    if (v == 4) return c->tma_ok && c->opts.iface == LB_IFACE_HERMITE;
     return v >= 0 && v < LB_NUM_VARIANTS;
 }
 
@@ -538,6 +579,8 @@ int step_t(lb_ctx *c, int64_t n)
         launch_variant<R>(c, c->variant, p);
         lbk::launch_iface<R>(c->store, p, c->stream);
         lbk::launch_pressure<R>(c->store, p, c->stream);
+        if (c->variant == 4 && !c->auxfix_h.empty())
+            lbk::launch_aux<R>(c->store, p, c->d_auxfix, (int)c->auxfix_h.size(), c->stream);
         if (int e = launch_check(c, "step")) return e;
         c->cur ^= 1;
         c->t = t_new;
@@ -647,6 +690,11 @@ bool make_maps(lb_ctx *c)
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
                 return false;
             if (enc(&c->maps[lv].box2[s], dt, 3, c->planes[lv][s], dims, strides, b2, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return false;
+            const cuuint32_t b5[3] = {(cuuint32_t)lbk::stream_cols(), (cuuint32_t)lbk::stream_rows() + 4, 1};
+            if (enc(&c->maps[lv].box5[s], dt, 3, c->planes[lv][s], dims, strides, b5, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
                 return false;
@@ -771,7 +819,11 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
     c->d_counter = static_cast<unsigned int *>(own(c, 256));
     c->d_uprev = own(c, (size_t)c->nx * c->ny * 2 * (use_f64(c) ? 8 : 4));
     c->d_err = static_cast<int *>(own(c, 256));
-    bool ok = c->d_tmap && c->d_part && c->d_out && c->d_counter && c->d_uprev && c->d_err;
+    const size_t rsize = use_f64(c) ? 8 : 4;
+    for (int lv = 0; lv < 2; ++lv) c->aux[lv] = own(c, 3 * (size_t)c->pitch * c->ny * rsize);
+    c->wall_num = own(c, 2 * (size_t)c->pitch * rsize);
+    bool ok = c->d_tmap && c->d_part && c->d_out && c->d_counter && c->d_uprev && c->d_err && c->aux[0] && c->aux[1] &&
+              c->wall_num;
     for (int lv = 0; lv < 2; ++lv)
         for (int s = 0; s < 2; ++s) ok = ok && c->planes[lv][s];
     if (!ok) {
@@ -1075,6 +1127,11 @@ int lb_state_load(lb_ctx *c, const void *src, size_t bytes)
     if (int e = cuda_check(c, cudaMemcpyAsync(c->planes[c->cur][1], s + c->set_bytes[0], c->set_bytes[1],
                                               cudaMemcpyHostToDevice, c->stream), "state load"))
         return e;
+    if (c->variant == 4) {   /* carried moments of the loaded level */
+        if (use_f64(c)) lbk::launch_aux<double>(c->store, make_params<double>(c, c->cur, c->cur, c->t), nullptr, 0, c->stream);
+        else lbk::launch_aux<float>(c->store, make_params<float>(c, c->cur, c->cur, c->t), nullptr, 0, c->stream);
+        if (int e = launch_check(c, "state load")) return e;
+    }
     return cuda_check(c, cudaStreamSynchronize(c->stream), "state load sync");
 }
 

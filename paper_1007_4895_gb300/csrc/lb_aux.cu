@@ -120,23 +120,6 @@ __global__ void moments_kernel(const __grid_constant__ StepParams<typename Store
 /* FP64 sums over every node: mass, |u - u_prev|^2, |u|^2, count of non-finite nodes.
  * Warp shuffles, then shared memory, then one partial per block; the last block to
  * finish adds the partials in block order (deterministic) and resets the counter. */
-template <int ST, int Q>
-__device__ __forceinline__ void node_moments(const typename Store<ST>::T *f, size_t plane,
-                                             const MomC<typename Store<ST>::R> *mc, typename Store<ST>::R rho0,
-                                             typename Store<ST>::R &rd, typename Store<ST>::R &jx,
-                                             typename Store<ST>::R &jy)
-{
-    using R = typename Store<ST>::R;
-    rd = jx = jy = R(0);
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        const R d = decode<ST>(f[a * plane], mc[a].winv, rho0);
-        rd = fma(mc[a].w, d, rd);
-        jx = fma(mc[a].wcx, d, jx);
-        jy = fma(mc[a].wcy, d, jy);
-    }
-}
-
 template <int ST>
 __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p,
                                                      typename Store<ST>::R *uprev, double *part, unsigned int *counter,

@@ -36,6 +36,25 @@ __device__ __forceinline__ void stage_consts(const StepParams<R> &p, PopC<R> (*p
     }
 }
 
+/* sum w d, sum w xi_x d, sum w xi_y d of one node's stored populations (f[a * plane])
+ * in population order: the moment pass of the step kernels. */
+template <int ST, int Q>
+__device__ __forceinline__ void node_moments(const typename Store<ST>::T *f, size_t plane,
+                                             const MomC<typename Store<ST>::R> *mc, typename Store<ST>::R rho0,
+                                             typename Store<ST>::R &rd, typename Store<ST>::R &jx,
+                                             typename Store<ST>::R &jy)
+{
+    using R = typename Store<ST>::R;
+    rd = jx = jy = R(0);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const R d = decode<ST>(f[a * plane], mc[a].winv, rho0);
+        rd = fma(mc[a].w, d, rd);
+        jx = fma(mc[a].wcx, d, jx);
+        jy = fma(mc[a].wcy, d, jy);
+    }
+}
+
 /* Row j + offset with ghost = wall node (Sec. 3.2) or a periodic image. |offset| <= 2. */
 template <typename R>
 __device__ __forceinline__ int row_at(const StepParams<R> &p, int j)

@@ -56,6 +56,12 @@ struct StepParams {
     const uint8_t *tmap;            /* [ny][ntx] tile flags */
     const void *fin[2];             /* planes of the level read, per set */
     void *fout[2];                  /* planes of the level written, per set */
+    /* carried moments (streamed layout): per node, in its own set, the sums
+     * sum w d, sum w xi_x d, sum w xi_y d of the stored deviations, R [3][ny][nx],
+     * of the level read (aux_in) and of the level written (aux_out) */
+    const void *aux_in;
+    void *aux_out;
+    void *wall_num;                 /* R [2][nx]: sum_out |xi.n| w d of each wall node */
     R rho0, dt;
     R kn_rho;                       /* kn_ref * rho_ref (tau = kn_rho / rho), or tau if const */
     int tau_const;                  /* 1: tau = kn_rho */
@@ -98,9 +104,19 @@ int launch_batch(int store, const void *params, const int *order, int n, int nst
                  unsigned int *queue, int threads, int grid, void *stream);
 /* resident blocks per SM of the batch kernel for a block size (0 on error) */
 int batch_blocks(int store, int threads);
+/* post-passes of the streamed layout, in order: diffuse-wall overwrite (+ its ghost
+ * rows), periodic ghost copies, (shadows, pressure: the kernels above), then carried
+ * moments of the listed quads (x0, j) recomputed from their final values */
+template <typename R>
+void launch_wall_post(int store, const StepParams<R> &p, void *stream);
+template <typename R>
+void launch_images(int store, const StepParams<R> &p, void *stream);
+template <typename R>
+void launch_aux(int store, const StepParams<R> &p, const int2 *list, int n, void *stream);
 /* step-kernel layouts: 0 one node quad per thread, 1 TMA-fed producer / consumer,
- * 2 and 3 split plain / edge kernels with register blocks of 4 x 1 and 4 x 2 nodes */
-#define LB_NUM_VARIANTS 4
+ * 2 and 3 split plain / edge kernels with register blocks of 4 x 1 and 4 x 2 nodes,
+ * 4 streamed (TMA, carried moments, boundary post-passes) */
+#define LB_NUM_VARIANTS 5
 
 /* The quad of nodes x0 .. x0+3 of row j needs none of the boundary work of the step
  * (wall overwrite, ghost-row or ghost-column copies, pressure column, mode-B shadow or

@@ -189,6 +189,116 @@ __global__ void shadows_kernel(const __grid_constant__ StepParams<typename Store
         put1r(p, ft + b * plane + (size_t)j * p.pitch, x, j, encode<ST>(hermite_rebuild(ct, b, h), ct.w[b], p.rho0));
 }
 
+/* ------------------------------------------- streamed-layout post-passes -- */
+
+/* Diffuse walls after the streamed kernel: f_out = rho_W S(u_W) for the gas-bound
+ * populations of each wall node (Sec. 3.2), from sum_out |xi.n| w dn that the kernel
+ * left in wall_num, in the arithmetic of step_cells; then the wall row's ghost rows. */
+template <int ST>
+__global__ void wall_post_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p)
+{
+    using T = typename Store<ST>::T;
+    using R = typename Store<ST>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, side = blockIdx.y;
+    if (x >= p.nx || !p.wall_diffuse[side]) return;
+    const int j = side == 0 ? 0 : p.ny - 1;
+    const int s = p.tmap[(size_t)j * p.ntx + x / LB_TILE_X] & LB_TILE_HIGH;
+    const SetConst<R> &c = p.set[s];
+    const size_t plane = p.plane;
+    const R rho0 = p.rho0, nsgn = side == 0 ? R(1) : R(-1);
+    const R uwx = p.uw_x[side], uwy = p.uw_y[side];
+    const R usw = uwx * uwx + uwy * uwy;
+    const R num = static_cast<const R *>(p.wall_num)[(size_t)side * p.pitch + x];
+    const R rwd = fma(rho0, p.kdiff[s][side], num) / p.kout[s][side];   /* rho_W - rho0 */
+    T *f = static_cast<T *>(p.fout[s]) + (size_t)j * p.pitch + x + LB_GHOST;
+    for (int a = 0; a < c.q; ++a) {
+        if (c.cy[a] * nsgn <= R(0)) continue;
+        const R ew = c.cx[a] * uwx + c.cy[a] * uwy;
+        const R sm1 = ew + R(0.5) * (ew * ew - usw);
+        f[a * plane] = encode<ST>(fma(rwd + rho0, sm1, rwd), c.w[a], rho0);
+    }
+    int img[2];
+    const int nimg = row_images(p, j, img);
+    for (int a = 0; a < c.q; ++a) {
+        const T e = f[a * plane];
+        for (int t = 0; t < nimg; ++t) f[a * plane + (ptrdiff_t)img[t] * p.pitch] = e;
+    }
+}
+
+/* Periodic ghost copies of every plane of both sets: the four ghost columns on each
+ * side of every storage row (periodic x) and the two ghost rows on each side of every
+ * storage column (periodic y). Reads of the stencil only ever use ghost columns of the
+ * logical rows and ghost rows of the logical columns, so the two copies are
+ * independent. blockIdx.y = plane (set 0 planes first). */
+template <int ST>
+__global__ void images_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p)
+{
+    using T = typename Store<ST>::T;
+    const int q0 = p.set[0].q;
+    const int s = (int)blockIdx.y < q0 ? 0 : 1;
+    const int a = (int)blockIdx.y - (s ? q0 : 0);
+    if (a >= p.set[s].q) return;
+    T *base = static_cast<T *>(p.fout[s]) + (size_t)a * p.plane - (size_t)LB_GHOST_ROWS * p.pitch;   /* storage row 0 */
+    const int rows = p.ny + 2 * LB_GHOST_ROWS;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p.periodic_x && k < rows * 2 * LB_GHOST) {
+        const int row = k / (2 * LB_GHOST), g = k % (2 * LB_GHOST);
+        T *r = base + (size_t)row * p.pitch;
+        if (g < LB_GHOST) r[g] = r[p.nx + g];                              /* node g - 4 <- node nx + g - 4 */
+        else r[p.nx + g] = r[g];                                           /* node nx + g - 4 <- node g - 4 */
+    }
+    if (p.periodic_y && k < p.pitch * 2 * LB_GHOST_ROWS) {
+        const int col = k % p.pitch, g = k / p.pitch;
+        if (g < LB_GHOST_ROWS) base[(size_t)g * p.pitch + col] = base[(size_t)(p.ny + g) * p.pitch + col];
+        else base[(size_t)(p.ny + g) * p.pitch + col] = base[(size_t)g * p.pitch + col];
+    }
+}
+
+/* Carried moments of the written level, sum w d, sum w xi_x d, sum w xi_y d per node
+ * from its stored populations in population order: of every node (list == NULL) or of
+ * the listed quads (x0, j). */
+template <int ST>
+__global__ void __launch_bounds__(128) aux_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p,
+                                                  const int2 *__restrict__ list, int n)
+{
+    using T = typename Store<ST>::T;
+    using R = typename Store<ST>::R;
+    __shared__ PopC<R> pcs[2][LB_QMAX];
+    __shared__ MomC<R> mcs[2][LB_QMAX];
+    stage_consts(p, pcs, mcs, threadIdx.x, blockDim.x);
+    __syncthreads();
+    int x, j, cnt;
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (list) {
+        if (k >= (size_t)n) return;
+        x = list[k].x;
+        j = list[k].y;
+        cnt = 4;
+    } else {
+        if (k >= (size_t)p.nx * p.ny) return;
+        j = (int)(k / p.nx);
+        x = (int)(k - (size_t)j * p.nx);
+        cnt = 1;
+    }
+    if (j < 0 || j >= p.ny) return;
+    R *aout = static_cast<R *>(p.aux_out);
+    const size_t ap = (size_t)p.pitch * p.ny;
+    for (int i = 0; i < cnt && x + i < p.nx; ++i) {
+        const int xi = x + i;
+        const int s = p.tmap[(size_t)j * p.ntx + xi / LB_TILE_X] & LB_TILE_HIGH;
+        const T *f = static_cast<const T *>(p.fout[s]) + (size_t)j * p.pitch + xi + LB_GHOST;
+        R rd, jx, jy;
+        const int q = p.set[s].q;
+        if (q == 9) node_moments<ST, 9>(f, p.plane, mcs[s], p.rho0, rd, jx, jy);
+        else if (q == 16) node_moments<ST, 16>(f, p.plane, mcs[s], p.rho0, rd, jx, jy);
+        else node_moments<ST, 36>(f, p.plane, mcs[s], p.rho0, rd, jx, jy);
+        const size_t m = (size_t)j * p.pitch + xi;
+        aout[m] = rd;
+        aout[ap + m] = jx;
+        aout[2 * ap + m] = jy;
+    }
+}
+
 /* ------------------------------------------------------------- launchers -- */
 
 template <typename R>
@@ -276,6 +386,43 @@ template void launch_step_split<float>(int, const StepParams<float> &, int, cons
 template void launch_step_split<double>(int, const StepParams<double> &, int, const int2 *, int, void *, void *);
 template void launch_iface<float>(int, const StepParams<float> &, void *);
 template void launch_iface<double>(int, const StepParams<double> &, void *);
+template <typename R>
+void launch_wall_post(int store, const StepParams<R> &p, void *stream)
+{
+    if (!p.wall_diffuse[0] && !p.wall_diffuse[1]) return;
+    dim3 grid((p.nx + 127) / 128, 2);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) wall_post_kernel<ST><<<grid, 128, 0, st>>>(p));
+}
+
+template <typename R>
+void launch_images(int store, const StepParams<R> &p, void *stream)
+{
+    if (!p.periodic_x && !p.periodic_y) return;
+    const long long nx_items = p.periodic_x ? (long long)(p.ny + 2 * LB_GHOST_ROWS) * 2 * LB_GHOST : 0;
+    const long long ny_items = p.periodic_y ? (long long)p.pitch * 2 * LB_GHOST_ROWS : 0;
+    const long long items = nx_items > ny_items ? nx_items : ny_items;
+    dim3 grid((unsigned)((items + 255) / 256), p.set[0].q + p.set[1].q);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) images_kernel<ST><<<grid, 256, 0, st>>>(p));
+}
+
+template <typename R>
+void launch_aux(int store, const StepParams<R> &p, const int2 *list, int n, void *stream)
+{
+    const long long items = list ? n : (long long)p.nx * p.ny;
+    if (items <= 0) return;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LB_DISPATCH(store, if constexpr (store_matches<R, ST>())
+                           aux_kernel<ST><<<(unsigned)((items + 127) / 128), 128, 0, st>>>(p, list, n));
+}
+
+template void launch_wall_post<float>(int, const StepParams<float> &, void *);
+template void launch_wall_post<double>(int, const StepParams<double> &, void *);
+template void launch_images<float>(int, const StepParams<float> &, void *);
+template void launch_images<double>(int, const StepParams<double> &, void *);
+template void launch_aux<float>(int, const StepParams<float> &, const int2 *, int, void *);
+template void launch_aux<double>(int, const StepParams<double> &, const int2 *, int, void *);
 template void launch_pressure<float>(int, const StepParams<float> &, void *);
 template void launch_pressure<double>(int, const StepParams<double> &, void *);
 template void launch_shadows<float>(int, const StepParams<float> &, void *);

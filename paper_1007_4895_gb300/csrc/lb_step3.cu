@@ -24,6 +24,7 @@
 #include <type_traits>
 
 #include "lb_common.cuh"
+#include "lb_tma.cuh"
 #include "lb_tma.h"
 
 namespace lbk {
@@ -33,56 +34,6 @@ namespace lbk {
 #define LB3_W 136                 /* columns per slot row: 128 + 4 halo on each side */
 #define LB3_NP 2                  /* population planes per slot */
 #define LB3_STAGES 8
-#define LB3_SPIN_LIMIT (1u << 24)
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0u;
-}
-
-/* bounded wait; on expiry sets *err (to `code`) and returns false */
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code)
-{
-    for (uint32_t it = 0; it < LB3_SPIN_LIMIT; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 1023u) == 1023u && *(volatile int *)err) return false;   /* another warp gave up */
-    }
-    atomicExch(err, code);
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
-        : "memory");
-}
 
 /* F_{k+1/2} - F_{k-1/2} along x for four nodes (Sec. 3.1), Courant number c (sign
  * decides the upwind side), limiter factor kf = (1 - |c|) / 2. */
@@ -437,7 +388,7 @@ __global__ void __launch_bounds__(32 * (LB3_NC + 1), 1) step3_kernel(const __gri
             const uint32_t first = it > LB3_STAGES ? it - LB3_STAGES : 0;
             for (uint32_t k = first; k < it; ++k) {
                 const int slot = k % LB3_STAGES;
-                for (uint32_t n = 0; n < LB3_SPIN_LIMIT && !mbar_try_wait(&full[slot], (k / LB3_STAGES) & 1u); ++n) {
+                for (uint32_t n = 0; n < LB_SPIN_LIMIT && !mbar_try_wait(&full[slot], (k / LB3_STAGES) & 1u); ++n) {
                 }
             }
         }

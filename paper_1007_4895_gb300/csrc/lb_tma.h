@@ -13,6 +13,7 @@
 struct TmaMaps {
     CUtensorMap box1[2];   /* per set: 136 columns x LB3_R rows x LB3_NP planes (a unit's rows) */
     CUtensorMap box2[2];   /* per set: 136 columns x (LB3_R + 4) rows x LB3_NP planes (plus the y halo) */
+    CUtensorMap box5[2];   /* per set: 136 columns x (stream rows + 4) rows x 1 plane (streamed layout) */
 };
 
 namespace lbk {
@@ -20,4 +21,9 @@ int launch_step3(int store, const StepParams<float> &p, const TmaMaps &maps, int
 int step3_rows();
 int step3_cols();
 int step3_planes();
+/* Streamed layout (4): TMA-fed single-pass kernel on carried moments (the boundary
+ * post-passes follow it). FP32 / FP16 / BF16 storage. 0 on launch, -1 if unavailable. */
+int launch_stream(int store, const StepParams<float> &p, const TmaMaps &maps, int *err, void *stream);
+int stream_rows();   /* rows per work unit */
+int stream_cols();   /* columns per plane tile: 128 + 2 x 4 ghost */
 }  // namespace lbk
