@@ -114,6 +114,31 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+def form_accuracy(lb, forms):
+    """Relative velocity error (max over nodes, C18) of each storage form against the
+    FP64 oracle on a steady force-driven channel (4 x 64, Kn 0.1, 32-row-per-wall
+    equivalent band of 10 rows, 6000 steps): the accuracy behind each form's throughput."""
+    import oracle
+    from lbinputs import poiseuille
+    w = poiseuille(nx=4, ny=64, rows=10, kn=0.1, g_lat=1e-5)
+    steps = 6000
+    out, ref = {}, None
+    for name, (store, rnd) in forms.items():
+        lat = lb.Lattice.from_workload(w, store=store, rounding=rnd, variant=0)
+        if ref is None:
+            o = oracle.Oracle(w.nx, w.ny, lat.effective_map(), kn_ref=w.kn_ref, gx=w.gx, walls=w.walls, dt=lat.dt,
+                              h=lat.h)
+            o.init_equilibrium(1.0, 0.0, 0.0)
+            o.step(steps)
+            ref = o.moments()
+        lat.step(steps)
+        m = lat.moments(mask=0b111)
+        du = np.sqrt((m["ux"] - ref["ux"]) ** 2 + (m["uy"] - ref["uy"]) ** 2)
+        out[name] = float(du.max() / np.sqrt(ref["ux"] ** 2 + ref["uy"] ** 2).max())
+        lat.close()
+    return out
+
+
 def cpu_baseline(seconds=12.0):
     """The FP64 oracle on one full-size channel of the sweep (Kn = 0.1), all host cores."""
     import oracle
@@ -167,8 +192,8 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def time_form(lb, torch, store, steps, warmup, variant=-1, with_kernel_times=True):
-    lats = [lb.Lattice.from_workload(w, store=store, variant=variant) for w in workloads()]
+def time_form(lb, torch, store, steps, warmup, variant=-1, with_kernel_times=True, rounding="nearest"):
+    lats = [lb.Lattice.from_workload(w, store=store, variant=variant, rounding=rounding) for w in workloads()]
     for _ in range(warmup):
         for lat in lats:
             lat.step(1)
@@ -302,13 +327,20 @@ def main():
 
     forms = {}
     if not args.no_forms:
-        for store in ("f32", "f16_dev", "bf16_dev"):
+        variants_of_forms = {"f32": ("f32", "nearest"), "f16_dev": ("f16_dev", "nearest"),
+                             "bf16_dev": ("bf16_dev", "nearest"), "f16_dev_sr": ("f16_dev", "stochastic"),
+                             "bf16_dev_sr": ("bf16_dev", "stochastic")}
+        for name, (store, rnd) in variants_of_forms.items():
             fs = max(50, min(args.steps, 1000))
-            tot, kern, nb, info = time_form(lb, torch, store, fs, 5, args.variant)
+            tot, kern, nb, info = time_form(lb, torch, store, fs, 5, args.variant, rounding=rnd)
             km = statistics.mean(kern)
-            forms[store] = {"value": cells * fs / (tot / 1e3) / 1e6, "unit": "MLUPS",
-                            "roofline_frac": (statistics.mean(nb) / (km / 1e3) / 1e9) / peak,
-                            "variant": info[0]["variant"]}
+            forms[name] = {"value": cells * fs / (tot / 1e3) / 1e6, "unit": "MLUPS",
+                           "roofline_frac": (statistics.mean(nb) / (km / 1e3) / 1e9) / peak,
+                           "variant": info[0]["variant"], "rounding": rnd}
+        acc = form_accuracy(lb, dict({"f32_dev": ("f32_dev", "nearest")}, **variants_of_forms))
+        for name, e in acc.items():
+            forms.setdefault(name, {})["e_u_vs_fp64_oracle"] = e
+        forms["accuracy_case"] = "steady Poiseuille 4x64, Kn 0.1, 6000 steps, max relative velocity error"
 
     line = {
         "metric": "coupled-LB MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,

@@ -145,7 +145,17 @@ typedef struct {
     void *(*alloc)(size_t bytes, void *user);
     void (*free)(void *ptr, void *user);
     void *alloc_user;
+    int32_t rounding;   /* LB_ROUND_NEAREST (0) or LB_ROUND_STOCHASTIC (1), see below */
 } lb_opts;
+
+/* Rounding of the updated populations into FP16 / BF16 deviation storage (other
+ * formats ignore it). Nearest (ties to even) loses every per-step increment smaller
+ * than half a unit in the last place of the stored deviation, so slow flows stagnate
+ * away from the solution; stochastic rounding (to the neighbour above or below with
+ * the probabilities that keep the expected stored value exact, random bits from a
+ * counter-based hash of node, population and step) keeps them on average. Values set
+ * by boundary rules are rounded to nearest. */
+enum { LB_ROUND_NEAREST = 0, LB_ROUND_STOCHASTIC = 1 };
 
 typedef struct lb_ctx lb_ctx;
 

@@ -19,6 +19,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbgb.so")
 
 LB_OK, LB_ERR_INVALID, LB_ERR_NOMEM, LB_ERR_CUDA, LB_ERR_DIVERGED, LB_ERR_TIMEOUT = range(6)
+LB_ROUND_NEAREST, LB_ROUND_STOCHASTIC = 0, 1
+ROUNDING = {"nearest": LB_ROUND_NEAREST, "stochastic": LB_ROUND_STOCHASTIC}
 LB_STORE_F64, LB_STORE_F32, LB_STORE_F32_DEV, LB_STORE_F16_DEV, LB_STORE_BF16_DEV = range(5)
 LB_IFACE_PAPER, LB_IFACE_HERMITE = 0, 1
 LB_WALL_PERIODIC, LB_WALL_DIFFUSE, LB_WALL_PRESSURE = 0, 1, 2
@@ -67,7 +69,7 @@ class lb_opts(ctypes.Structure):
                 ("gx", ctypes.c_double), ("gy", ctypes.c_double), ("reduce_every", ctypes.c_int32),
                 ("variant", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_user", ctypes.c_void_p)]
+                ("alloc_user", ctypes.c_void_p), ("rounding", ctypes.c_int32)]
 
 
 def _load():
@@ -355,7 +357,7 @@ class Lattice:
 
     def __init__(self, nx, ny, region_map, sets=(9, 36), kn_ref=0.1, rho_ref=1.0, tau_mode=0, walls=None,
                  store="f32", iface="hermite", rho0=1.0, gx=0.0, gy=0.0, cfl=0.5, dt=0.0, h=0.0,
-                 reduce_every=0, stream=None, torch_allocator=True, variant=-1):
+                 reduce_every=0, stream=None, torch_allocator=True, variant=-1, rounding="nearest"):
         self.nx, self.ny = int(nx), int(ny)
         self.sets = tuple(int(s) for s in sets)
         self.store = STORES[store] if isinstance(store, str) else int(store)
@@ -371,6 +373,7 @@ class Lattice:
         opts.rho0, opts.gx, opts.gy = rho0, gx, gy
         opts.reduce_every = int(reduce_every)
         opts.variant = int(variant)
+        opts.rounding = ROUNDING[rounding] if isinstance(rounding, str) else int(rounding)
         opts.stream = sp
         if torch_allocator:
             self._alloc = _TorchAllocator(stream)

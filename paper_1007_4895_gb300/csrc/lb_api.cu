@@ -194,6 +194,9 @@ StepParams<R> make_params(const lb_ctx *c, int in, int out, double t_new)
         p.fout[s] = static_cast<char *>(c->planes[out][s]) + row0;
     }
     p.plane = (size_t)(c->ny + 2 * LB_GHOST_ROWS) * c->pitch;
+    p.sr = (c->opts.rounding == LB_ROUND_STOCHASTIC &&
+            (c->store == LB_STORE_F16_DEV || c->store == LB_STORE_BF16_DEV)) ? 1 : 0;
+    p.step_key = (uint32_t)(c->step + (in != out ? 1 : 0));
     p.aux_in = c->aux[in];
     p.aux_out = c->aux[out];
     p.wall_num = c->wall_num;
@@ -750,6 +753,8 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
     if (opts->store < LB_STORE_F64 || opts->store > LB_STORE_BF16_DEV) return fail(LB_ERR_INVALID, "unknown storage");
     if (opts->iface != LB_IFACE_PAPER && opts->iface != LB_IFACE_HERMITE) return fail(LB_ERR_INVALID, "unknown interface mode");
     if (opts->variant >= LB_NUM_VARIANTS) return fail(LB_ERR_INVALID, "unknown kernel variant");
+    if (opts->rounding != LB_ROUND_NEAREST && opts->rounding != LB_ROUND_STOCHASTIC)
+        return fail(LB_ERR_INVALID, "unknown rounding mode");
     if (!(opts->rho0 > 0.0)) return fail(LB_ERR_INVALID, "rho0 must be positive");
     for (int k = 0; k < 4; ++k)
         if (walls[k].kind < LB_WALL_PERIODIC || walls[k].kind > LB_WALL_PRESSURE)
@@ -1277,6 +1282,8 @@ int batch_upload_params(lb_batch *b)
         const lb_ctx *c = b->inst[i];
         h[2 * (size_t)i] = make_params<R>(c, c->cur, c->cur ^ 1, c->t + c->dt);
         h[2 * (size_t)i + 1] = make_params<R>(c, c->cur ^ 1, c->cur, c->t + 2.0 * c->dt);
+        /* the parameters serve every step of a launch: no per-step random key */
+        h[2 * (size_t)i].sr = h[2 * (size_t)i + 1].sr = 0;
     }
     b->d_params = batch_alloc(b, h.size() * sizeof(StepParams<R>));
     if (!b->d_params) return fail(LB_ERR_NOMEM, "device allocation failed");

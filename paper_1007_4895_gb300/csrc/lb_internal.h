@@ -62,6 +62,8 @@ struct StepParams {
     const void *aux_in;
     void *aux_out;
     void *wall_num;                 /* R [2][nx]: sum_out |xi.n| w d of each wall node */
+    int sr;                         /* stochastic rounding of the updated populations */
+    uint32_t step_key;              /* the step being computed (random-bit key) */
     R rho0, dt;
     R kn_rho;                       /* kn_ref * rho_ref (tau = kn_rho / rho), or tau if const */
     int tau_const;                  /* 1: tau = kn_rho */

@@ -172,10 +172,12 @@ __device__ __forceinline__ void consume_set(const Tma3Params<ST> &P, int s, int 
     int img[2];
     const int nimg = mine ? row_images(p, j, img) : 0;
 
-    auto store_quad = [&](T *dst, const R dn[4], R w) {
+    auto store_quad = [&](T *dst, const R dn[4], R w, int a) {
         T e[4];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) e[m] = encode<ST>(dn[m], w, rho0);
+        for (int m = 0; m < 4; ++m)
+            e[m] = (a >= 0 && p.sr) ? encode_sr<ST>(dn[m], w, rho0, sr_bits(x0 + m, j, p.nx, a, p.step_key))
+                                    : encode<ST>(dn[m], w, rho0);
         for (int t = -1; t < nimg; ++t) {
             T *d = t < 0 ? dst : dst + (ptrdiff_t)img[t] * p.pitch;
             if (full_row && !edge) {
@@ -277,7 +279,7 @@ __device__ __forceinline__ void consume_set(const Tma3Params<ST> &P, int s, int 
                         for (int m = 0; m < 4; ++m) num[m] = fma(-xn * pc.w, dn[m], num[m]);
                     }
                 }
-                store_quad(fout + a * plane, dn, pc.w);
+                store_quad(fout + a * plane, dn, pc.w, a);
             }
         }
         __syncwarp();
@@ -301,7 +303,7 @@ __device__ __forceinline__ void consume_set(const Tma3Params<ST> &P, int s, int 
             R dn[4];
 #pragma unroll
             for (int m = 0; m < 4; ++m) dn[m] = fma(rwd[m] + rho0, sm1, rwd[m]);
-            store_quad(fout + a * plane, dn, c.w[a]);
+            store_quad(fout + a * plane, dn, c.w[a], -1);
         }
     }
 

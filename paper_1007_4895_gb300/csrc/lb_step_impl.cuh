@@ -153,10 +153,14 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
 
     int img[2];
     const int nimg = row_images(p, j, img);
-    auto store_quad = [&](T *dst, const R dn[4], R w) {
+    /* a >= 0: an updated population (stochastically rounded when p.sr); a < 0: a value
+     * set by the wall (rounded to nearest) */
+    auto store_quad = [&](T *dst, const R dn[4], R w, int a) {
         T e[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) e[k] = encode<ST>(dn[k], w, rho0);
+        for (int k = 0; k < 4; ++k)
+            e[k] = (a >= 0 && p.sr) ? encode_sr<ST>(dn[k], w, rho0, sr_bits(x0 + k, j, p.nx, a, p.step_key))
+                                    : encode<ST>(dn[k], w, rho0);
         for (int t = -1; t < nimg; ++t) {
             T *d = t < 0 ? dst : dst + (ptrdiff_t)img[t] * p.pitch;
             if (full && !near_x_edge) {
@@ -249,7 +253,7 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
                     for (int k = 0; k < 4; ++k) num[k] = fma(-xn * pc.w, dn[k], num[k]);
                 }
             }
-            store_quad(fout + a * plane + row0, dn, pc.w);
+            store_quad(fout + a * plane + row0, dn, pc.w, a);
         }
 
     } else {
@@ -342,7 +346,7 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
                     for (int k = 0; k < 4; ++k) num[k] = fma(-xn * pc.w, dn[k], num[k]);
                 }
             }
-            if (!replaced) store_quad(fout + a * plane + row0, dn, pc.w);
+            if (!replaced) store_quad(fout + a * plane + row0, dn, pc.w, a);
             if constexpr (PF) {
                 cur = nxt;
                 pcur = pnxt;
@@ -368,7 +372,7 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
             /* rho_W S / w - rho0 = (rho_W - rho0)(1 + sm1) + rho0 sm1 */
 #pragma unroll
             for (int k = 0; k < 4; ++k) dn[k] = fma(rwd[k] + rho0, sm1, rwd[k]);
-            store_quad(fout + a * plane + row0, dn, c.w[a]);
+            store_quad(fout + a * plane + row0, dn, c.w[a], -1);
         }
     }
 
@@ -607,7 +611,8 @@ __device__ __forceinline__ void blk_cells(const StepParams<typename Store<ST>::R
                     const R eu = cxa * ux[r][k] + cya * uy[r][k];
                     t = fma(p.dt * rho[r][k], gxi + gxi * eu - gu[r][k], t);
                 }
-                e[k] = encode<ST>(v[r][k] + t, pc.w, rho0);
+                e[k] = p.sr ? encode_sr<ST>(v[r][k] + t, pc.w, rho0, sr_bits(x0 + k, j0 + r, p.nx, a, p.step_key))
+                            : encode<ST>(v[r][k] + t, pc.w, rho0);
             }
             st4(fout + a * plane + r * pitch, e);
         }

@@ -92,6 +92,66 @@ __device__ __forceinline__ typename Store<ST>::T encode(typename Store<ST>::R d,
     }
 }
 
+/* ---- stochastic rounding of the 16-bit deviation formats ----
+ * A per-step increment below half a unit in the last place of the stored deviation is
+ * lost by round-to-nearest every step, and the state stagnates away from the solution.
+ * Rounding up or down with the probabilities that make the expected stored value equal
+ * the exact one keeps those increments on average. The random bits come from a
+ * counter-based generator: C. Wellons' "lowbias32" integer hash (xorshift-multiply
+ * finaliser, published 2018) of a key naming the node, the population and the step, so
+ * every kernel layout draws the same bits for the same store. */
+__device__ __forceinline__ uint32_t lowbias32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t sr_bits(int x, int j, int nx, int a, uint32_t step)
+{
+    return lowbias32(lowbias32((uint32_t)j * (uint32_t)nx + (uint32_t)x) ^ lowbias32(((uint32_t)a << 24) ^ step));
+}
+
+/* BF16 is the upper half of FP32: adding 16 random bits below the kept half and
+ * truncating carries into it with probability equal to the dropped fraction (of the
+ * magnitude: the pattern is sign-magnitude). */
+__device__ __forceinline__ __nv_bfloat16 sr_bf16(float v, uint32_t r)
+{
+    uint32_t b = __float_as_uint(v);
+    if ((b & 0x7f800000u) == 0x7f800000u) return __float2bfloat16_rn(v);   /* inf, nan */
+    b += r & 0xffffu;
+    __nv_bfloat16_raw raw;
+    raw.x = (unsigned short)(b >> 16);
+    return __nv_bfloat16(raw);
+}
+
+/* FP16: the neighbour toward zero and the next code away from zero bracket v; the
+ * latter is taken with probability (v - lo) / (hi - lo). */
+__device__ __forceinline__ __half sr_half(float v, uint32_t r)
+{
+    const __half lo = __float2half_rz(v);
+    const float lof = __half2float(lo);
+    if (!(fabsf(v) < 65504.0f) || lof == v) return __float2half_rn(v);
+    const __half hi = __ushort_as_half((unsigned short)(__half_as_ushort(lo) + 1u));
+    const float frac = (v - lof) / (__half2float(hi) - lof);
+    const float u = (float)(r >> 8) * (1.0f / 16777216.0f);
+    return u < frac ? hi : lo;
+}
+
+/* deviation -> stored value, stochastically rounded for the 16-bit formats (r: random
+ * bits), as encode() otherwise */
+template <int ST>
+__device__ __forceinline__ typename Store<ST>::T encode_sr(typename Store<ST>::R d, typename Store<ST>::R w,
+                                                          typename Store<ST>::R rho0, uint32_t r)
+{
+    if constexpr (ST == 3) return sr_half(d, r);
+    else if constexpr (ST == 4) return sr_bf16(d, r);
+    else return encode<ST>(d, w, rho0);
+}
+
 /* Four consecutive elements (16-byte aligned for FP32, 32 for FP64, 8 for 16-bit). */
 template <typename T>
 __device__ __forceinline__ void ld4(const T *p, T v[4]);

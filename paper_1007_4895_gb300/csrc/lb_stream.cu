@@ -214,7 +214,9 @@ __device__ __forceinline__ void stream_set(const Stream5Params<ST> &P, int s, in
                 }
                 T e[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) e[k] = encode<ST>(dn[k], pc.w, rho0);
+                for (int k = 0; k < 4; ++k)
+                    e[k] = p.sr ? encode_sr<ST>(dn[k], pc.w, rho0, sr_bits(x0 + k, jt + r, p.nx, a, p.step_key))
+                                : encode<ST>(dn[k], pc.w, rho0);
                 T *dst = fout + (size_t)a * plane + (size_t)r * p.pitch;
                 if (full_quad) {
                     st4(dst, e);

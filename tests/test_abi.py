@@ -50,12 +50,14 @@ def _args(lb, nx=8, ny=8, **over):
         walls[k] = v
     opts = lb.lb_opts()
     opts.store, opts.iface, opts.rho0 = over.get("store", 1), over.get("iface", 1), over.get("rho0", 1.0)
+    opts.rounding = over.get("rounding", 0)
     return grid, np.zeros((ny, nx), np.uint8), over.get("sets", (9, 36)), kn, walls, opts
 
 
 @pytest.mark.parametrize("case", [
     dict(nx=2), dict(ny=3), dict(sets=(9, 25)), dict(store=9), dict(iface=5), dict(rho0=0.0), dict(kn=-1.0),
     dict(kn=1e-6),                                  # dt / tau > 1
+    dict(rounding=2),                               # unknown rounding mode
     dict(walls={0: None}),                          # bottom periodic, top diffuse (filled below)
 ])
 def test_invalid_arguments_are_rejected_on_the_host(lb, case):

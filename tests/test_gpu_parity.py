@@ -203,6 +203,63 @@ def test_reduced_precision_channel(store):
         assert errs[k] < b, (k, errs)
 
 
+# Stochastic rounding of the 16-bit stores (lb_opts.rounding): the expected stored value
+# equals the exact one, so increments below half an ulp are kept on average and the
+# stagnation bias above disappears; what remains is rounding noise of about one ulp of
+# the deviation per node. Bounds from the measured noise with a 3x margin.
+SR_BOUNDS = {"f16_dev": {"u": 1e-3, "rho": 2e-4, "pxy": 5e-3},
+             "bf16_dev": {"u": 1.2e-2, "rho": 1.5e-3, "pxy": 3e-2}}
+
+
+def _box(n=64, g=1e-3):
+    walls = {"bottom": {"kind": "periodic"}, "top": {"kind": "periodic"}}
+    return Workload(name="forced_box", nx=n, ny=n, region_map=np.zeros((n, n), np.uint8), kn_ref=0.1, walls=walls,
+                    gx=g, steps=4000)
+
+
+@pytest.mark.parametrize("store", ["f16_dev", "bf16_dev"])
+def test_stochastic_rounding_keeps_small_increments(store):
+    """A periodic box at rest under a uniform body force gains momentum at exactly
+    rho g per unit time (the force moments, Eq. (demoforce)), so u = g t. Rounding to
+    nearest drops the per-step gain once it falls below half an ulp of the stored
+    deviation (BF16 stalls for good); stochastic rounding keeps the mean on g t."""
+    import paper_1007_4895_gb300 as lb
+    res = {}
+    for rnd in ("nearest", "stochastic"):
+        w = _box()
+        lat = lb.Lattice.from_workload(w, store=store, rounding=rnd)
+        lat.step(w.steps)
+        exact = w.gx * lat.info()["time"]
+        res[rnd] = abs(lat.moments(mask=0b111)["ux"].mean() - exact) / exact
+    assert res["nearest"] > (0.5 if store == "bf16_dev" else 2e-2), res
+    assert res["stochastic"] < 1e-3, res
+
+
+@pytest.mark.parametrize("store", ["f16_dev", "bf16_dev"])
+@pytest.mark.parametrize("flow", ["couette", "poiseuille"])
+def test_stochastic_rounding_channels_match_oracle(store, flow):
+    if flow == "couette":
+        w, n = couette(nx=4, ny=32, rows=4, kn=0.1, u_wall_lat=0.05), 5000
+    else:
+        w, n = poiseuille(nx=4, ny=64, rows=10, kn=0.1, g_lat=1e-5), 6000
+    import paper_1007_4895_gb300 as lb
+    import oracle
+    from gpu_pair import N1D
+    errs = {}
+    for rnd in ("nearest", "stochastic"):
+        lat = lb.Lattice.from_workload(w, store=store, rounding=rnd)
+        eff = lat.effective_map()
+        o = oracle.Oracle(w.nx, w.ny, eff, n1d_lo=N1D[w.sets[0]], n1d_hi=N1D[w.sets[1]], kn_ref=w.kn_ref,
+                          rho_ref=w.rho_ref, gx=w.gx, walls=w.walls, dt=lat.dt, h=lat.h)
+        o.init_equilibrium(w.rho0, 0.0, 0.0)
+        lat.step(n)
+        o.step(n)
+        errs[rnd] = field_errors(lat.moments(), o.moments())
+    for k, b in SR_BOUNDS[store].items():
+        assert errs["stochastic"][k] < b, (k, errs["stochastic"])
+    assert errs["stochastic"]["u"] < 0.1 * errs["nearest"]["u"], errs
+
+
 # ------------------------------------------------- full-size launch shapes
 
 def test_poiseuille_full_size_columns_match_oracle():
@@ -235,15 +292,24 @@ def test_long_channel_every_layout_matches_oracle(variant):
     assert errs["u"] < F32_VEL_TOL and errs["rho"] < F32_VEL_TOL, errs
 
 
-@pytest.mark.parametrize("store", ["f64", "f32_dev", "bf16_dev"])
+@pytest.mark.parametrize("store", ["f64", "f32_dev", "bf16_dev", "bf16_dev_sr", "f16_dev_sr"])
 @pytest.mark.parametrize("variant", [2, 3, 4])
 def test_register_block_layouts_equal_quad_layout(store, variant):
-    """The register-block layouts do the quad layout's arithmetic in the same order, so
-    their populations agree with it bit for bit (walls, force, periodic edges, a ragged
-    tile and interface tiles fall back to the quad path inside the same launch)."""
-    w = ragged_workload()
-    a, _, _ = make_pair(w, store=store, variant=0)
-    b, _, _ = make_pair(ragged_workload(), store=store, variant=variant)
+    """The split and streamed layouts do the quad layout's arithmetic in the same order,
+    and draw the same random bits when rounding stochastically, so their populations
+    agree with it bit for bit (walls, force, periodic edges, a ragged tile and interface
+    tiles)."""
+    import paper_1007_4895_gb300 as lb
+    rnd = "stochastic" if store.endswith("_sr") else "nearest"
+    st = store.replace("_sr", "")
+
+    def build(v):
+        w = ragged_workload()
+        lat = lb.Lattice.from_workload(w, store=st, variant=v, rounding=rnd)
+        return lat, None, None
+
+    a, _, _ = build(0)
+    b, _, _ = build(variant)
     a.step(40)
     b.step(40)
     for s in (0, 1):
