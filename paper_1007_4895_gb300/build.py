@@ -47,8 +47,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC", "-I", CSRC,
-                     "--expt-relaxed-constexpr"]
+    # -fmad=false: no implicit multiply-add contraction. The step layouts evaluate the
+    # same expressions in differently shaped code, and the compiler's choice of which
+    # product to fuse depends on that shape; with contraction off every layout rounds
+    # alike and the fused products are the explicit fma() calls of the source. The host
+    # side likewise (-ffp-contract=off), so that host-computed constants are the same
+    # on x86-64 and AArch64.
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", CSRC,
+                     "--expt-relaxed-constexpr", "-fmad=false"]
     if verbose:
         common += ["-Xptxas", "-v"]
 

@@ -92,13 +92,12 @@ struct lb_ctx {
     int2 *d_edge[2] = {nullptr, nullptr};
     size_t edge_cap[2] = {0, 0};
     cudaStream_t edge_stream = nullptr;   /* the edge kernel runs here, overlapping */
-    /* streamed layout: carried moments per level, wall sums, quads whose carried
-     * moments are recomputed after the boundary post-passes */
+    /* streamed layout: carried moments per level and work units */
     void *aux[2] = {nullptr, nullptr};
-    void *wall_num = nullptr;
-    std::vector<int2> auxfix_h;
-    int2 *d_auxfix = nullptr;
-    size_t auxfix_cap = 0;
+    std::vector<int4> units_h;      /* (tile, first row, rows, set) runs, most work first */
+    int4 *d_units = nullptr;
+    size_t units_cap = 0;
+    unsigned int *d_squeue = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     /* learned placement */
     lb_mlp *mlp = nullptr;
@@ -199,7 +198,6 @@ StepParams<R> make_params(const lb_ctx *c, int in, int out, double t_new)
     p.step_key = (uint32_t)(c->step + (in != out ? 1 : 0));
     p.aux_in = c->aux[in];
     p.aux_out = c->aux[out];
-    p.wall_num = c->wall_num;
     p.rho0 = R(c->opts.rho0);
     p.dt = R(c->dt);
     p.tau_const = c->kn.rho_ref > 0.0 ? 0 : 1;
@@ -371,25 +369,34 @@ int build_edge_lists(lb_ctx *c)
                                                   c->stream), "edge list upload"))
             return e;
     }
-    /* quads rewritten after the streamed kernel: diffuse-wall rows, pressure columns */
-    std::vector<int2> &A = c->auxfix_h;
-    A.clear();
-    for (int j = 0; j < c->ny; ++j) {
-        const bool wall_row = (j == 0 && c->walls[0].kind == LB_WALL_DIFFUSE) ||
-                              (j == c->ny - 1 && c->walls[1].kind == LB_WALL_DIFFUSE);
-        for (int x0 = 0; x0 < c->nx; x0 += 4)
-            if (wall_row || (pl && x0 == 0) || (ph && x0 + 3 >= c->nx - 1)) A.push_back(make_int2(x0, j));
-    }
-    if (!A.empty()) {
-        if (A.size() > c->auxfix_cap) {
-            const size_t cap = std::max(A.size(), 2 * c->auxfix_cap);
-            int2 *d = static_cast<int2 *>(own(c, cap * sizeof(int2)));
-            if (!d) return fail(LB_ERR_NOMEM, "device allocation failed");
-            c->d_auxfix = d;
-            c->auxfix_cap = cap;
+    /* work units of the streamed layout: runs of one set in a tile column, at most
+     * stream_rows() rows each, most work (populations x rows) first */
+    std::vector<int4> &U = c->units_h;
+    U.clear();
+    const int th = lbk::stream_rows();
+    for (int tx = 0; tx < c->ntx; ++tx) {
+        int j = 0;
+        while (j < c->ny) {
+            const int s = c->tmap[(size_t)j * c->ntx + tx] & LB_TILE_HIGH;
+            int k = j;
+            while (k < c->ny && k - j < th && (c->tmap[(size_t)k * c->ntx + tx] & LB_TILE_HIGH) == s) ++k;
+            U.push_back(make_int4(tx, j, k - j, s));
+            j = k;
         }
-        if (int e = cuda_check(c, cudaMemcpyAsync(c->d_auxfix, A.data(), A.size() * sizeof(int2), cudaMemcpyHostToDevice,
-                                                  c->stream), "fix-up list upload"))
+    }
+    std::stable_sort(U.begin(), U.end(), [&](const int4 &a, const int4 &b) {
+        return (long long)c->q[a.w] * a.z > (long long)c->q[b.w] * b.z;
+    });
+    if (!U.empty()) {
+        if (U.size() > c->units_cap) {
+            const size_t cap = std::max(U.size(), 2 * c->units_cap);
+            int4 *d = static_cast<int4 *>(own(c, cap * sizeof(int4)));
+            if (!d) return fail(LB_ERR_NOMEM, "device allocation failed");
+            c->d_units = d;
+            c->units_cap = cap;
+        }
+        if (int e = cuda_check(c, cudaMemcpyAsync(c->d_units, U.data(), U.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                                  c->stream), "unit list upload"))
             return e;
     }
     return LB_OK;
@@ -415,10 +422,9 @@ void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
             return;
     }
     if constexpr (std::is_same<R, float>::value) {
-        if (variant == 4 && c->tma_ok && lbk::launch_stream(c->store, p, c->maps[c->cur], c->d_err, c->stream) == 0) {
-            lbk::launch_wall_post<R>(c->store, p, c->stream);
-            lbk::launch_images<R>(c->store, p, c->stream);
-            if (c->opts.iface == LB_IFACE_HERMITE) lbk::launch_shadows<R>(c->store, p, c->stream);
+        if (variant == 4 && c->tma_ok &&
+            lbk::launch_stream(c->store, p, c->maps[c->cur], c->d_units, (int)c->units_h.size(), c->d_squeue, c->d_err,
+                               c->stream) == 0) {
             return;
         }
     }
@@ -582,8 +588,6 @@ int step_t(lb_ctx *c, int64_t n)
         launch_variant<R>(c, c->variant, p);
         lbk::launch_iface<R>(c->store, p, c->stream);
         lbk::launch_pressure<R>(c->store, p, c->stream);
-        if (c->variant == 4 && !c->auxfix_h.empty())
-            lbk::launch_aux<R>(c->store, p, c->d_auxfix, (int)c->auxfix_h.size(), c->stream);
         if (int e = launch_check(c, "step")) return e;
         c->cur ^= 1;
         c->t = t_new;
@@ -826,9 +830,9 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
     c->d_err = static_cast<int *>(own(c, 256));
     const size_t rsize = use_f64(c) ? 8 : 4;
     for (int lv = 0; lv < 2; ++lv) c->aux[lv] = own(c, 3 * (size_t)c->pitch * c->ny * rsize);
-    c->wall_num = own(c, 2 * (size_t)c->pitch * rsize);
+    c->d_squeue = static_cast<unsigned int *>(own(c, 256));
     bool ok = c->d_tmap && c->d_part && c->d_out && c->d_counter && c->d_uprev && c->d_err && c->aux[0] && c->aux[1] &&
-              c->wall_num;
+              c->d_squeue;
     for (int lv = 0; lv < 2; ++lv)
         for (int s = 0; s < 2; ++s) ok = ok && c->planes[lv][s];
     if (!ok) {

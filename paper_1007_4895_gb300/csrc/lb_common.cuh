@@ -76,7 +76,30 @@ __device__ __forceinline__ bool is_pressure_node(const StepParams<R> &p, int x, 
 template <typename R>
 __device__ __forceinline__ R deq(R rhod, R rho, R eu, R usq)
 {
-    return rhod + rho * (eu + R(0.5) * (eu * eu - usq));
+    return fma(rho, fma(R(0.5), fma(eu, eu, -usq), eu), rhod);
+}
+
+/* The library is compiled without implicit multiply-add contraction, so that every
+ * layout rounds the same expression the same way; the products below are fused where
+ * the source says so, in one place for all layouts. */
+/* xi . u */
+template <typename R>
+__device__ __forceinline__ R xi_dot(R cx, R cy, R ux, R uy)
+{
+    return fma(cy, uy, cx * ux);
+}
+/* u . u */
+template <typename R>
+__device__ __forceinline__ R usq_of(R ux, R uy)
+{
+    return fma(uy, uy, ux * ux);
+}
+/* Eq. (demoforce) increment of one population: dt rho [g.xi + (g.xi)(xi.u) - g.u],
+ * added to t; gxi = g.xi, gu = g.u */
+template <typename R>
+__device__ __forceinline__ R force_inc(R dt_rho, R gxi, R eu, R gu, R t)
+{
+    return fma(dt_rho, fma(gxi, eu, gxi) - gu, t);
 }
 
 template <typename R>

@@ -61,7 +61,6 @@ struct StepParams {
      * of the level read (aux_in) and of the level written (aux_out) */
     const void *aux_in;
     void *aux_out;
-    void *wall_num;                 /* R [2][nx]: sum_out |xi.n| w d of each wall node */
     int sr;                         /* stochastic rounding of the updated populations */
     uint32_t step_key;              /* the step being computed (random-bit key) */
     R rho0, dt;
@@ -106,13 +105,8 @@ int launch_batch(int store, const void *params, const int *order, int n, int nst
                  unsigned int *queue, int threads, int grid, void *stream);
 /* resident blocks per SM of the batch kernel for a block size (0 on error) */
 int batch_blocks(int store, int threads);
-/* post-passes of the streamed layout, in order: diffuse-wall overwrite (+ its ghost
- * rows), periodic ghost copies, (shadows, pressure: the kernels above), then carried
- * moments of the listed quads (x0, j) recomputed from their final values */
-template <typename R>
-void launch_wall_post(int store, const StepParams<R> &p, void *stream);
-template <typename R>
-void launch_images(int store, const StepParams<R> &p, void *stream);
+/* carried moments (streamed layout) of every node of the written level (list == NULL)
+ * or of the listed quads (x0, j), from their stored populations */
 template <typename R>
 void launch_aux(int store, const StepParams<R> &p, const int2 *list, int n, void *stream);
 /* step-kernel layouts: 0 one node quad per thread, 1 TMA-fed producer / consumer,

@@ -140,6 +140,24 @@ __global__ void pressure_kernel(const __grid_constant__ StepParams<typename Stor
         };
         if (h0) put(a0, d0);
         if (h1) put(a1, d1);
+        /* carried moments of the node (streamed layout): its final populations summed in
+         * population order, as the moment pass of the step kernels does */
+        const T e0 = h0 ? f[a0 * plane + xb] : T(0), e1 = h1 ? f[a1 * plane + xb] : T(0);
+        R sr = R(0), sx = R(0), sy = R(0);
+        for (int a = 0; a < q; ++a) {
+            const T e = __shfl_sync(0xffffffffu, a < 32 ? e0 : e1, a & 31);
+            const R d = decode<ST>(e, c.winv[a], rho0);
+            sr = fma(c.w[a], d, sr);
+            sx = fma(c.wcx[a], d, sx);
+            sy = fma(c.wcy[a], d, sy);
+        }
+        if (lane == 0 && p.aux_out) {
+            R *aout = static_cast<R *>(p.aux_out);
+            const size_t ap = (size_t)p.pitch * p.ny, m = (size_t)j * p.pitch + xb;
+            aout[m] = sr;
+            aout[ap + m] = sx;
+            aout[2 * ap + m] = sy;
+        }
     }
     /* ghost columns, and the node's second-order Hermite coefficients for a shadow */
     R hc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
@@ -189,70 +207,7 @@ __global__ void shadows_kernel(const __grid_constant__ StepParams<typename Store
         put1r(p, ft + b * plane + (size_t)j * p.pitch, x, j, encode<ST>(hermite_rebuild(ct, b, h), ct.w[b], p.rho0));
 }
 
-/* ------------------------------------------- streamed-layout post-passes -- */
-
-/* Diffuse walls after the streamed kernel: f_out = rho_W S(u_W) for the gas-bound
- * populations of each wall node (Sec. 3.2), from sum_out |xi.n| w dn that the kernel
- * left in wall_num, in the arithmetic of step_cells; then the wall row's ghost rows. */
-template <int ST>
-__global__ void wall_post_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p)
-{
-    using T = typename Store<ST>::T;
-    using R = typename Store<ST>::R;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, side = blockIdx.y;
-    if (x >= p.nx || !p.wall_diffuse[side]) return;
-    const int j = side == 0 ? 0 : p.ny - 1;
-    const int s = p.tmap[(size_t)j * p.ntx + x / LB_TILE_X] & LB_TILE_HIGH;
-    const SetConst<R> &c = p.set[s];
-    const size_t plane = p.plane;
-    const R rho0 = p.rho0, nsgn = side == 0 ? R(1) : R(-1);
-    const R uwx = p.uw_x[side], uwy = p.uw_y[side];
-    const R usw = uwx * uwx + uwy * uwy;
-    const R num = static_cast<const R *>(p.wall_num)[(size_t)side * p.pitch + x];
-    const R rwd = fma(rho0, p.kdiff[s][side], num) / p.kout[s][side];   /* rho_W - rho0 */
-    T *f = static_cast<T *>(p.fout[s]) + (size_t)j * p.pitch + x + LB_GHOST;
-    for (int a = 0; a < c.q; ++a) {
-        if (c.cy[a] * nsgn <= R(0)) continue;
-        const R ew = c.cx[a] * uwx + c.cy[a] * uwy;
-        const R sm1 = ew + R(0.5) * (ew * ew - usw);
-        f[a * plane] = encode<ST>(fma(rwd + rho0, sm1, rwd), c.w[a], rho0);
-    }
-    int img[2];
-    const int nimg = row_images(p, j, img);
-    for (int a = 0; a < c.q; ++a) {
-        const T e = f[a * plane];
-        for (int t = 0; t < nimg; ++t) f[a * plane + (ptrdiff_t)img[t] * p.pitch] = e;
-    }
-}
-
-/* Periodic ghost copies of every plane of both sets: the four ghost columns on each
- * side of every storage row (periodic x) and the two ghost rows on each side of every
- * storage column (periodic y). Reads of the stencil only ever use ghost columns of the
- * logical rows and ghost rows of the logical columns, so the two copies are
- * independent. blockIdx.y = plane (set 0 planes first). */
-template <int ST>
-__global__ void images_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p)
-{
-    using T = typename Store<ST>::T;
-    const int q0 = p.set[0].q;
-    const int s = (int)blockIdx.y < q0 ? 0 : 1;
-    const int a = (int)blockIdx.y - (s ? q0 : 0);
-    if (a >= p.set[s].q) return;
-    T *base = static_cast<T *>(p.fout[s]) + (size_t)a * p.plane - (size_t)LB_GHOST_ROWS * p.pitch;   /* storage row 0 */
-    const int rows = p.ny + 2 * LB_GHOST_ROWS;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p.periodic_x && k < rows * 2 * LB_GHOST) {
-        const int row = k / (2 * LB_GHOST), g = k % (2 * LB_GHOST);
-        T *r = base + (size_t)row * p.pitch;
-        if (g < LB_GHOST) r[g] = r[p.nx + g];                              /* node g - 4 <- node nx + g - 4 */
-        else r[p.nx + g] = r[g];                                           /* node nx + g - 4 <- node g - 4 */
-    }
-    if (p.periodic_y && k < p.pitch * 2 * LB_GHOST_ROWS) {
-        const int col = k % p.pitch, g = k / p.pitch;
-        if (g < LB_GHOST_ROWS) base[(size_t)g * p.pitch + col] = base[(size_t)(p.ny + g) * p.pitch + col];
-        else base[(size_t)(p.ny + g) * p.pitch + col] = base[(size_t)g * p.pitch + col];
-    }
-}
+/* ------------------------------------------------------ carried moments -- */
 
 /* Carried moments of the written level, sum w d, sum w xi_x d, sum w xi_y d per node
  * from its stored populations in population order: of every node (list == NULL) or of
@@ -386,26 +341,8 @@ template void launch_step_split<float>(int, const StepParams<float> &, int, cons
 template void launch_step_split<double>(int, const StepParams<double> &, int, const int2 *, int, void *, void *);
 template void launch_iface<float>(int, const StepParams<float> &, void *);
 template void launch_iface<double>(int, const StepParams<double> &, void *);
-template <typename R>
-void launch_wall_post(int store, const StepParams<R> &p, void *stream)
-{
-    if (!p.wall_diffuse[0] && !p.wall_diffuse[1]) return;
-    dim3 grid((p.nx + 127) / 128, 2);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) wall_post_kernel<ST><<<grid, 128, 0, st>>>(p));
-}
 
-template <typename R>
-void launch_images(int store, const StepParams<R> &p, void *stream)
-{
-    if (!p.periodic_x && !p.periodic_y) return;
-    const long long nx_items = p.periodic_x ? (long long)(p.ny + 2 * LB_GHOST_ROWS) * 2 * LB_GHOST : 0;
-    const long long ny_items = p.periodic_y ? (long long)p.pitch * 2 * LB_GHOST_ROWS : 0;
-    const long long items = nx_items > ny_items ? nx_items : ny_items;
-    dim3 grid((unsigned)((items + 255) / 256), p.set[0].q + p.set[1].q);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) images_kernel<ST><<<grid, 256, 0, st>>>(p));
-}
+
 
 template <typename R>
 void launch_aux(int store, const StepParams<R> &p, const int2 *list, int n, void *stream)
@@ -417,10 +354,6 @@ void launch_aux(int store, const StepParams<R> &p, const int2 *list, int n, void
                            aux_kernel<ST><<<(unsigned)((items + 127) / 128), 128, 0, st>>>(p, list, n));
 }
 
-template void launch_wall_post<float>(int, const StepParams<float> &, void *);
-template void launch_wall_post<double>(int, const StepParams<double> &, void *);
-template void launch_images<float>(int, const StepParams<float> &, void *);
-template void launch_images<double>(int, const StepParams<double> &, void *);
 template void launch_aux<float>(int, const StepParams<float> &, const int2 *, int, void *);
 template void launch_aux<double>(int, const StepParams<double> &, const int2 *, int, void *);
 template void launch_pressure<float>(int, const StepParams<float> &, void *);

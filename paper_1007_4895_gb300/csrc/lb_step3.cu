@@ -158,7 +158,7 @@ __device__ __forceinline__ void consume_set(const Tma3Params<ST> &P, int s, int 
         const R inv = R(1) / rho[m];
         ux[m] *= inv;
         uy[m] *= inv;
-        usq[m] = ux[m] * ux[m] + uy[m] * uy[m];
+        usq[m] = usq_of(ux[m], uy[m]);
         om[m] = p.dt / tau_of(p, rho[m]);
     }
 
@@ -257,17 +257,17 @@ __device__ __forceinline__ void consume_set(const Tma3Params<ST> &P, int s, int 
                 }
                 R dn[4];
                 const R cxa = pc.cx, cya = pc.cy;
-                const R gxi = p.gx * cxa + p.gy * cya;
+                const R gxi = xi_dot(cxa, cya, p.gx, p.gy);
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
-                    const R eu = fma(cya, uy[m], cxa * ux[m]);
+                    const R eu = xi_dot(cxa, cya, ux[m], uy[m]);
                     const R de = deq(rhod[m], rho[m], eu, usq[m]);
                     R inc = om[m] * (de - v[m]);
                     inc = fma(-crx, Dx[m], inc);
                     inc = fma(-cry, Dy[m], inc);
                     if (p.has_force) {
-                        const R gu = fma(p.gy, uy[m], p.gx * ux[m]);
-                        inc = fma(p.dt * rho[m], gxi + gxi * eu - gu, inc);
+                        const R gu = xi_dot(p.gx, p.gy, ux[m], uy[m]);
+                        inc = force_inc(p.dt * rho[m], gxi, eu, gu, inc);
                     }
                     dn[m] = v[m] + inc;
                 }

@@ -131,9 +131,9 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
         R inv = R(1) / rho[k];
         ux[k] = jx[k] * inv;
         uy[k] = jy[k] * inv;
-        usq[k] = ux[k] * ux[k] + uy[k] * uy[k];
+        usq[k] = usq_of(ux[k], uy[k]);
         om[k] = p.dt / tau_of(p, rho[k]);
-        gu[k] = p.gx * ux[k] + p.gy * uy[k];
+        gu[k] = xi_dot(p.gx, p.gy, ux[k], uy[k]);
     }
 
     int wall = -1;
@@ -233,16 +233,16 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
             }
             R dn[4];
             const R cxa = pc.cx, cya = pc.cy;
-            const R gxi = p.gx * cxa + p.gy * cya;
+            const R gxi = xi_dot(cxa, cya, p.gx, p.gy);
     #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                R eu = cxa * ux[k] + cya * uy[k];
+                R eu = xi_dot(cxa, cya, ux[k], uy[k]);
                 R de = deq(rhod[k], rho[k], eu, usq[k]);
                 /* sum the small increments first and round onto the stored magnitude once */
                 R inc = om[k] * (de - v[k]);
                 inc = fma(-crx, Dx[k], inc);
                 inc = fma(-cry, Dy[k], inc);
-                if (p.has_force) inc = fma(p.dt * rho[k], gxi + gxi * eu - gu[k], inc);
+                if (p.has_force) inc = force_inc(p.dt * rho[k], gxi, eu, gu[k], inc);
                 dn[k] = v[k] + inc;
             }
             if (wall >= 0) {
@@ -325,16 +325,16 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
             }
             R dn[4];
             const R cxa = pc.cx, cya = pc.cy;
-            const R gxi = p.gx * cxa + p.gy * cya;
+            const R gxi = xi_dot(cxa, cya, p.gx, p.gy);
     #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                R eu = cxa * ux[k] + cya * uy[k];
+                R eu = xi_dot(cxa, cya, ux[k], uy[k]);
                 R de = deq(rhod[k], rho[k], eu, usq[k]);
                 /* sum the small increments first and round onto the stored magnitude once */
                 R inc = om[k] * (de - v[k]);
                 inc = fma(-crx, Dx[k], inc);
                 inc = fma(-cry, Dy[k], inc);
-                if (p.has_force) inc = fma(p.dt * rho[k], gxi + gxi * eu - gu[k], inc);
+                if (p.has_force) inc = force_inc(p.dt * rho[k], gxi, eu, gu[k], inc);
                 dn[k] = v[k] + inc;
             }
             bool replaced = false;   /* wall-bound population on a wall row: written below */
@@ -509,9 +509,9 @@ __device__ __forceinline__ void blk_cells(const StepParams<typename Store<ST>::R
             const R inv = R(1) / rho[r][k];
             ux[r][k] *= inv;
             uy[r][k] *= inv;
-            usq[r][k] = ux[r][k] * ux[r][k] + uy[r][k] * uy[r][k];
+            usq[r][k] = usq_of(ux[r][k], uy[r][k]);
             om[r][k] = p.dt / tau_of(p, rho[r][k]);
-            if constexpr (FORCE) gu[r][k] = p.gx * ux[r][k] + p.gy * uy[r][k];
+            if constexpr (FORCE) gu[r][k] = xi_dot(p.gx, p.gy, ux[r][k], uy[r][k]);
         }
 
     /* 3. per population: stencil (loaded one population ahead), fluxes, collision,
@@ -560,7 +560,7 @@ __device__ __forceinline__ void blk_cells(const StepParams<typename Store<ST>::R
         for (int r = 0; r < RB; ++r)
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const R eu = cxa * ux[r][k] + cya * uy[r][k];
+                const R eu = xi_dot(cxa, cya, ux[r][k], uy[r][k]);
                 inc[r][k] = om[r][k] * (deq(rhod[r][k], rho[r][k], eu, usq[r][k]) - v[r][k]);
             }
         if (crx != R(0)) {
@@ -600,7 +600,7 @@ __device__ __forceinline__ void blk_cells(const StepParams<typename Store<ST>::R
                 for (int r = 0; r < RB; ++r) inc[r][k] = fma(-cry, Dy[r], inc[r][k]);
             }
         }
-        const R gxi = p.gx * cxa + p.gy * cya;
+        const R gxi = xi_dot(cxa, cya, p.gx, p.gy);
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
             T e[4];
@@ -608,8 +608,8 @@ __device__ __forceinline__ void blk_cells(const StepParams<typename Store<ST>::R
             for (int k = 0; k < 4; ++k) {
                 R t = inc[r][k];
                 if constexpr (FORCE) {
-                    const R eu = cxa * ux[r][k] + cya * uy[r][k];
-                    t = fma(p.dt * rho[r][k], gxi + gxi * eu - gu[r][k], t);
+                    const R eu = xi_dot(cxa, cya, ux[r][k], uy[r][k]);
+                    t = force_inc(p.dt * rho[r][k], gxi, eu, gu[r][k], t);
                 }
                 e[k] = p.sr ? encode_sr<ST>(v[r][k] + t, pc.w, rho0, sr_bits(x0 + k, j0 + r, p.nx, a, p.step_key))
                             : encode<ST>(v[r][k] + t, pc.w, rho0);

@@ -6,18 +6,24 @@
  *   - the moments of level n are not summed again at step n: the step that wrote level
  *     n left, per node, sum w d, sum w xi_x d and sum w xi_y d of the values it stored
  *     (aux_in); this step sums them for level n+1 as it stores (aux_out);
- *   - one producer warp streams, for each work unit (128 columns x LB5_TH rows) and each
- *     population plane, the unit's rows plus two halo rows on each side and four ghost
- *     columns on each side into a ring of shared-memory slots with
- *     cp.async.bulk.tensor, each slot guarded by a full / empty mbarrier pair;
+ *   - work units are runs of at most LB5_TH rows of one set in one 128-column tile
+ *     (built on the host, most work first); one producer warp per block takes units
+ *     from a global queue and streams, for each population plane, the unit's rows plus
+ *     two halo rows and four ghost columns on each side into a ring of shared-memory
+ *     slots with cp.async.bulk.tensor, each slot guarded by a full / empty mbarrier
+ *     pair and headed by the unit it belongs to;
  *   - each consumer thread owns 4 columns x LB5_RB rows, reads its radius-2 cross from
  *     the slot (the limited slope of a face between its two rows is formed once) and
  *     writes the new populations to global memory in 16-byte vectors.
- * The kernel does no boundary work: no ghost copies, shadow rebuilds or pressure
- * columns, and on a diffuse wall row it leaves the gas-bound populations to the wall
- * post-pass, to which it hands sum_out |xi.n| w dn (lb_step.cu). Every mbarrier wait is
- * bounded; on expiry the block records the failure in an error word, waits (bounded)
- * for the copies it issued, and returns.
+ * The boundary work of step_cells is done here too, with the same arithmetic: periodic
+ * ghost columns with every store; at the end of a unit the diffuse-wall overwrite (the
+ * wall row's moments are then summed again, in population order, from its final values,
+ * and its ghost rows written), the ghost rows of periodic-y edge rows, and the mode-B
+ * rebuild of shadow nodes from the Hermite sums of their final values (summed as they
+ * are stored). Pressure columns are left to the pressure pass, which also writes their
+ * carried moments. Every mbarrier wait is bounded; on expiry
+ * the block records the failure in an error word, waits (bounded) for the copies it
+ * issued, and returns.
  */
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -45,24 +51,39 @@ template <int ST>
 struct Stream5Params {
     StepParams<typename Store<ST>::R> p;
     int *err;
+    const int4 *units;      /* (tile, first row, rows, set), most work first */
     int nunits;
-    CUtensorMap map[2];   /* per set: box 136 x (LB5_TH + 4) x 1 */
+    unsigned int *queue;    /* next unit to take; zero at launch */
+    CUtensorMap map[2];     /* per set: box 136 x (LB5_TH + 4) x 1 */
 };
 
-/* sets (bit s) that rows j0 .. j0 + LB5_TH - 1 use */
-template <typename R>
-__device__ __forceinline__ int unit_sets5(const StepParams<R> &p, int tile, int j0)
+/* dynamic shared memory: LB5_STAGES slots, full and empty barriers, slot headers, then
+ * three side sums per node of each consumer thread (R [RB * 4 * 3][LB5_NC * 32]) */
+template <int ST>
+__host__ __device__ constexpr size_t stream_xs_offset5()
 {
-    int sets = 0;
-    for (int r = 0; r < LB5_TH && j0 + r < p.ny; ++r) sets |= 1 << (p.tmap[(size_t)(j0 + r) * p.ntx + tile] & LB_TILE_HIGH);
-    return sets;
+    return (size_t)LB5_STAGES * slot_bytes5<ST>() + 2 * LB5_STAGES * sizeof(uint64_t) + LB5_STAGES * sizeof(int);
+}
+template <int ST>
+__host__ __device__ constexpr size_t smem_bytes5()
+{
+    return stream_xs_offset5<ST>() + (size_t)LB5_RB * 4 * 3 * LB5_NC * 32 * sizeof(typename Store<ST>::R);
 }
 
+/* second-order Hermite weights of one population: w (xi_x^2-1), w xi_x xi_y, w (xi_y^2-1) */
+template <typename R>
+struct alignas(4 * sizeof(R)) HerC {
+    R wxx, wxy, wyy, pad;
+};
+
+/* One unit (tile, rows j0 .. j0 + nrows - 1 of set s) over its Q population slots; the
+ * slot of population 0 has already been waited for. */
 template <int ST, int Q, bool FORCE>
-__device__ __forceinline__ void stream_set(const Stream5Params<ST> &P, int s, int tile, int j0, uint8_t *smem_base,
-                                           uint64_t *full, uint64_t *empty, uint32_t &it, bool &alive,
-                                           const PopC<typename Store<ST>::R> *pcs,
-                                           const MomC<typename Store<ST>::R> *mcs)
+__device__ __forceinline__ void stream_set(const Stream5Params<ST> &P, int s, int tile, int j0, int nrows,
+                                           uint8_t *smem_base, uint64_t *full, uint64_t *empty, uint32_t &it,
+                                           bool &alive, const PopC<typename Store<ST>::R> *pcs,
+                                           const MomC<typename Store<ST>::R> *mcs,
+                                           const HerC<typename Store<ST>::R> *hcs)
 {
     using T = typename Store<ST>::T;
     using R = typename Store<ST>::R;
@@ -76,54 +97,123 @@ __device__ __forceinline__ void stream_set(const Stream5Params<ST> &P, int s, in
     const R rho0 = p.rho0;
     const size_t ap = (size_t)p.pitch * p.ny;   /* carried-moment plane */
 
-    bool own[RB], wall_row[RB], any = false;
-    int wall[RB];
+    bool own[RB], wall_row[RB], shadow[RB], any = false;
+    int wall[RB], nimg[RB], img0[RB], img1[RB];
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
         const int j = jt + r;
-        own[r] = alive && j < p.ny && x0 < p.nx && ((p.tmap[(size_t)j * p.ntx + tile] & LB_TILE_HIGH) == s);
+        const uint8_t flags = (j < p.ny) ? p.tmap[(size_t)j * p.ntx + tile] : 0;
+        own[r] = alive && j < j0 + nrows && j < p.ny && x0 < p.nx && ((flags & LB_TILE_HIGH) == s);
         wall[r] = -1;
         if (own[r] && j == 0 && p.wall_diffuse[0]) wall[r] = 0;
         if (own[r] && j == p.ny - 1 && p.wall_diffuse[1]) wall[r] = 1;
         wall_row[r] = wall[r] >= 0;
+        shadow[r] = own[r] && (flags & LB_TILE_SHADOW);
+        int im[2] = {0, 0};
+        nimg[r] = own[r] ? row_images(p, j, im) : 0;
+        img0[r] = im[0];
+        img1[r] = im[1];
         any = any || own[r];
     }
-    bool valid[4];
+    /* nodes this thread stores: inside the lattice and not a pressure column (set by the
+     * pressure pass; the corner nodes of a diffuse wall are wall nodes) */
+    bool valid[RB][4], full_quad[RB];
+    const bool near_x_edge = p.periodic_x && (x0 < LB_GHOST || x0 + 3 >= p.nx - LB_GHOST);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) valid[k] = x0 + k < p.nx;
-    const bool full_quad = valid[3];
+    for (int r = 0; r < RB; ++r) {
+        full_quad[r] = !near_x_edge;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            valid[r][k] = own[r] && x0 + k < p.nx && !is_pressure_node(p, x0 + k, jt + r);
+            full_quad[r] = full_quad[r] && valid[r][k];
+        }
+    }
 
     /* carried moments of level n -> state of the collision */
     R rhod[RB][4], ux[RB][4], uy[RB][4], rho[RB][4], usq[RB][4], om[RB][4], gu[RB][4];
     const R *ain = static_cast<const R *>(p.aux_in);
 #pragma unroll
-    for (int r = 0; r < RB; ++r)
+    for (int r = 0; r < RB; ++r) {
+        const size_t n = (size_t)(jt + r) * p.pitch + x0;
+        R jx[4], jy[4];
+        if (full_quad[r]) {
+            ld4(ain + n, rhod[r]);
+            ld4(ain + ap + n, jx);
+            ld4(ain + 2 * ap + n, jy);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const bool ok = valid[r][k];
+                rhod[r][k] = ok ? ain[n + k] : R(0);
+                jx[k] = ok ? ain[ap + n + k] : R(0);
+                jy[k] = ok ? ain[2 * ap + n + k] : R(0);
+            }
+        }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const bool ok = own[r] && valid[k];
-            const size_t n = (size_t)(jt + r) * p.pitch + x0 + k;
-            rhod[r][k] = ok ? ain[n] : R(0);
-            const R jx = ok ? ain[ap + n] : R(0), jy = ok ? ain[2 * ap + n] : R(0);
             rho[r][k] = rho0 + rhod[r][k];
             const R inv = R(1) / rho[r][k];
-            ux[r][k] = jx * inv;
-            uy[r][k] = jy * inv;
-            usq[r][k] = ux[r][k] * ux[r][k] + uy[r][k] * uy[r][k];
+            ux[r][k] = jx[k] * inv;
+            uy[r][k] = jy[k] * inv;
+            usq[r][k] = usq_of(ux[r][k], uy[r][k]);
             om[r][k] = p.dt / tau_of(p, rho[r][k]);
-            if constexpr (FORCE) gu[r][k] = p.gx * ux[r][k] + p.gy * uy[r][k];
+            if constexpr (FORCE) gu[r][k] = xi_dot(p.gx, p.gy, ux[r][k], uy[r][k]);
         }
-    R nr[RB][4], nx_[RB][4], ny_[RB][4], num[RB][4];
+    }
+    /* sums of level n+1 over the values as stored: nr, nx_, ny_ = sum w d, w xi_x d,
+     * w xi_y d (the carried moments, and the first three Hermite coefficients of a
+     * shadow); ex = sum_out |xi.n| w dn on a wall row, or the three second-order Hermite
+     * sums w (xi_x^2-1) d, w xi_x xi_y d, w (xi_y^2-1) d on a shadow row */
+    R nr[RB][4], nx_[RB][4], ny_[RB][4];
+    bool hsum[RB];
+    /* ex lives in shared memory (few rows need it), one column per consumer thread */
+    R *xs = reinterpret_cast<R *>(smem_base + stream_xs_offset5<ST>()) + threadIdx.x;
+#define LB5_EX(r, k, m) xs[(((r) * 4 + (k)) * 3 + (m)) * (LB5_NC * 32)]
 #pragma unroll
-    for (int r = 0; r < RB; ++r)
+    for (int r = 0; r < RB; ++r) {
+        hsum[r] = shadow[r] && !wall_row[r];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) nr[r][k] = nx_[r][k] = ny_[r][k] = num[r][k] = R(0);
+        for (int k = 0; k < 4; ++k) {
+            nr[r][k] = nx_[r][k] = ny_[r][k] = R(0);
+            if (wall_row[r] || hsum[r]) LB5_EX(r, k, 0) = LB5_EX(r, k, 1) = LB5_EX(r, k, 2) = R(0);
+        }
+    }
 
     T *fout = static_cast<T *>(p.fout[s]) + (size_t)jt * p.pitch + (x0 + LB_GHOST);
+    /* a row's four values (with their periodic ghost columns); the ghost-row copies of a
+     * wall row or of a periodic-y edge row are written once its values are final, at
+     * the end of the unit */
+    auto store_one = [&](T *d, int r, const T e[4]) {
+        if (full_quad[r]) {
+            st4(d, e);
+        } else {
+            T *prow = d - (x0 + LB_GHOST);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (valid[r][k]) put1(p, prow, x0 + k, e[k]);
+        }
+    };
+    auto store_images = [&](T *dst, int r, const T e[4]) {
+        if (nimg[r] > 0) store_one(dst + (ptrdiff_t)img0[r] * p.pitch, r, e);
+        if (nimg[r] > 1) store_one(dst + (ptrdiff_t)img1[r] * p.pitch, r, e);
+    };
+    auto store_row = [&](T *dst, int r, const T e[4]) {
+        store_one(dst, r, e);
+        store_images(dst, r, e);
+    };
+    auto load_one = [&](const T *f, int r, T raw[4]) {
+        if (full_quad[r]) {
+            ld4(f, raw);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) raw[k] = valid[r][k] ? f[k] : T();
+        }
+    };
 
 #pragma unroll 1
     for (int a = 0; a < Q; ++a, ++it) {
         const int slot = it % LB5_STAGES;
-        if (alive) alive = mbar_wait(&full[slot], (it / LB5_STAGES) & 1u, P.err, 1);
+        if (alive && a > 0) alive = mbar_wait(&full[slot], (it / LB5_STAGES) & 1u, P.err, 1);
         if (alive && any) {
             const PopC<R> pc = pcs[a];
             const R winv = pc.winv, crx = pc.crx, cry = pc.cry, cxa = pc.cx, cya = pc.cy;
@@ -142,7 +232,7 @@ __device__ __forceinline__ void stream_set(const Stream5Params<ST> &P, int s, in
             for (int r = 0; r < RB; ++r)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const R eu = cxa * ux[r][k] + cya * uy[r][k];
+                    const R eu = xi_dot(cxa, cya, ux[r][k], uy[r][k]);
                     inc[r][k] = om[r][k] * (deq(rhod[r][k], rho[r][k], eu, usq[r][k]) - v[r][k]);
                 }
             if (crx != R(0)) {
@@ -190,7 +280,7 @@ __device__ __forceinline__ void stream_set(const Stream5Params<ST> &P, int s, in
                     for (int r = 0; r < RB; ++r) inc[r][k] = fma(-cry, Dy[r], inc[r][k]);
                 }
             }
-            const R gxi = p.gx * cxa + p.gy * cya;
+            const R gxi = xi_dot(cxa, cya, p.gx, p.gy);
 #pragma unroll
             for (int r = 0; r < RB; ++r) {
                 if (!own[r]) continue;
@@ -199,8 +289,8 @@ __device__ __forceinline__ void stream_set(const Stream5Params<ST> &P, int s, in
                 for (int k = 0; k < 4; ++k) {
                     R t = inc[r][k];
                     if constexpr (FORCE) {
-                        const R eu = cxa * ux[r][k] + cya * uy[r][k];
-                        t = fma(p.dt * rho[r][k], gxi + gxi * eu - gu[r][k], t);
+                        const R eu = xi_dot(cxa, cya, ux[r][k], uy[r][k]);
+                        t = force_inc(p.dt * rho[r][k], gxi, eu, gu[r][k], t);
                     }
                     dn[k] = v[r][k] + t;
                 }
@@ -209,7 +299,7 @@ __device__ __forceinline__ void stream_set(const Stream5Params<ST> &P, int s, in
                     if (xn > R(0)) continue;   /* gas-bound: written by the wall post-pass */
                     if (xn < R(0)) {
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) num[r][k] = fma(-xn * pc.w, dn[k], num[r][k]);
+                        for (int k = 0; k < 4; ++k) LB5_EX(r, k, 0) = fma(-xn * pc.w, dn[k], LB5_EX(r, k, 0));
                     }
                 }
                 T e[4];
@@ -217,14 +307,7 @@ __device__ __forceinline__ void stream_set(const Stream5Params<ST> &P, int s, in
                 for (int k = 0; k < 4; ++k)
                     e[k] = p.sr ? encode_sr<ST>(dn[k], pc.w, rho0, sr_bits(x0 + k, jt + r, p.nx, a, p.step_key))
                                 : encode<ST>(dn[k], pc.w, rho0);
-                T *dst = fout + (size_t)a * plane + (size_t)r * p.pitch;
-                if (full_quad) {
-                    st4(dst, e);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (valid[k]) dst[k] = e[k];
-                }
+                store_one(fout + (size_t)a * plane + (size_t)r * p.pitch, r, e);
                 /* moments of level n+1 from the values as stored, in population order
                  * and with the constants of the one-quad layout's moment pass */
                 const MomC<R> mcon = mcs[a];
@@ -235,25 +318,117 @@ __device__ __forceinline__ void stream_set(const Stream5Params<ST> &P, int s, in
                     nx_[r][k] = fma(mcon.wcx, d, nx_[r][k]);
                     ny_[r][k] = fma(mcon.wcy, d, ny_[r][k]);
                 }
+                if (hsum[r]) {
+                    const HerC<R> hcon = hcs[a];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const R d = decode<ST>(e[k], mcon.winv, rho0);
+                        LB5_EX(r, k, 0) = fma(hcon.wxx, d, LB5_EX(r, k, 0));
+                        LB5_EX(r, k, 1) = fma(hcon.wxy, d, LB5_EX(r, k, 1));
+                        LB5_EX(r, k, 2) = fma(hcon.wyy, d, LB5_EX(r, k, 2));
+                    }
+                }
             }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);
     }
     if (!alive) return;
-    R *aout = static_cast<R *>(p.aux_out);
-    R *wnum = static_cast<R *>(p.wall_num);
+    const SetConst<R> &c = p.set[s];
+    /* diffuse wall: f_out = rho_W S(u_W) with zero net mass flux, as step_cells part 4;
+     * then the wall row's sums again from all its final values in population order */
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
-        if (!own[r]) continue;
+        if (!wall_row[r]) continue;
+        const int wl = wall[r];
+        const R nsgn = wl == 0 ? R(1) : R(-1);
+        const R uwx = p.uw_x[wl], uwy = p.uw_y[wl];
+        const R usw = uwx * uwx + uwy * uwy;
+        const R kd = p.kdiff[s][wl], kout = p.kout[s][wl];
+        R rwd[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rwd[k] = fma(rho0, kd, LB5_EX(r, k, 0)) / kout;
+#pragma unroll 1
+        for (int a = 0; a < Q; ++a) {
+            if (c.cy[a] * nsgn <= R(0)) continue;
+            const R ew = c.cx[a] * uwx + c.cy[a] * uwy;
+            const R sm1 = ew + R(0.5) * (ew * ew - usw);
+            T e[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) e[k] = encode<ST>(fma(rwd[k] + rho0, sm1, rwd[k]), c.w[a], rho0);
+            store_one(fout + (size_t)a * plane + (size_t)r * p.pitch, r, e);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) nr[r][k] = nx_[r][k] = ny_[r][k] = LB5_EX(r, k, 0) = LB5_EX(r, k, 1) = LB5_EX(r, k, 2) = R(0);
+#pragma unroll 4
+        for (int a = 0; a < Q; ++a) {
+            T *f = fout + (size_t)a * plane + (size_t)r * p.pitch;
+            T raw[4];
+            load_one(f, r, raw);
+            store_images(f, r, raw);
+            const MomC<R> mcon = mcs[a];
+            const HerC<R> hcon = hcs[a];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const R d = decode<ST>(raw[k], mcon.winv, rho0);
+                nr[r][k] = fma(mcon.w, d, nr[r][k]);
+                nx_[r][k] = fma(mcon.wcx, d, nx_[r][k]);
+                ny_[r][k] = fma(mcon.wcy, d, ny_[r][k]);
+                if (shadow[r]) {
+                    LB5_EX(r, k, 0) = fma(hcon.wxx, d, LB5_EX(r, k, 0));
+                    LB5_EX(r, k, 1) = fma(hcon.wxy, d, LB5_EX(r, k, 1));
+                    LB5_EX(r, k, 2) = fma(hcon.wyy, d, LB5_EX(r, k, 2));
+                }
+            }
+        }
+    }
+    /* ghost-row copies of the other rows that have them (periodic y) */
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+        if (wall_row[r] || nimg[r] == 0) continue;
+#pragma unroll 4
+        for (int a = 0; a < Q; ++a) {
+            T *f = fout + (size_t)a * plane + (size_t)r * p.pitch;
+            T raw[4];
+            load_one(f, r, raw);
+            store_images(f, r, raw);
+        }
+    }
+    /* mode B: the node as the other set's readers will see it, as step_cells part 5,
+     * from the Hermite sums of its final values */
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+        if (!shadow[r]) continue;
+        const SetConst<R> &ct = p.set[1 - s];
+        T *ftd = static_cast<T *>(p.fout[1 - s]) + (size_t)(jt + r) * p.pitch + (x0 + LB_GHOST);
+#pragma unroll 1
+        for (int b = 0; b < ct.q; ++b) {
+            T e[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const R h[6] = {nr[r][k], nx_[r][k], ny_[r][k], LB5_EX(r, k, 0), LB5_EX(r, k, 1), LB5_EX(r, k, 2)};
+                e[k] = encode<ST>(hermite_rebuild(ct, b, h), ct.w[b], rho0);
+            }
+            store_row(ftd + (size_t)b * plane, r, e);
+        }
+    }
+#undef LB5_EX
+    R *aout = static_cast<R *>(p.aux_out);
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
         const size_t n = (size_t)(jt + r) * p.pitch + x0;
+        if (full_quad[r]) {
+            st4(aout + n, nr[r]);
+            st4(aout + ap + n, nx_[r]);
+            st4(aout + 2 * ap + n, ny_[r]);
+            continue;
+        }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            if (!valid[k]) continue;
+            if (!valid[r][k]) continue;
             aout[n + k] = nr[r][k];
             aout[ap + n + k] = nx_[r][k];
             aout[2 * ap + n + k] = ny_[r][k];
-            if (wall_row[r]) wnum[(size_t)wall[r] * p.pitch + x0 + k] = num[r][k];
         }
     }
 }
@@ -267,11 +442,18 @@ __global__ void __launch_bounds__(32 * (LB5_NC + 1), 1) stream_kernel(const __gr
     constexpr size_t SLOTB = slot_bytes5<ST>();
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)LB5_STAGES * SLOTB);
     uint64_t *empty = full + LB5_STAGES;
+    int *head = reinterpret_cast<int *>(empty + LB5_STAGES);   /* unit of each slot */
     const StepParams<R> &p = P.p;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ PopC<R> pc[2][LB_QMAX];
     __shared__ MomC<R> mc[2][LB_QMAX];
+    __shared__ HerC<R> hc[2][LB_QMAX];
     stage_consts(p, pc, mc, threadIdx.x, blockDim.x);
+    for (int i = threadIdx.x; i < 2 * LB_QMAX; i += blockDim.x) {
+        const int st = i / LB_QMAX, a = i % LB_QMAX;
+        const SetConst<R> &c = p.set[st];
+        if (a < c.q) hc[st][a] = HerC<R>{c.wxx[a], c.wxy[a], c.wyy[a], R(0)};
+    }
     if (threadIdx.x == 0) {
         for (int k = 0; k < LB5_STAGES; ++k) {
             mbar_init(&full[k], 1);
@@ -282,26 +464,30 @@ __global__ void __launch_bounds__(32 * (LB5_NC + 1), 1) stream_kernel(const __gr
     __syncthreads();
 
     if (warp == LB5_NC) {
-        /* producer */
+        /* producer: takes units from the queue; slot header = unit index, -1 = no more */
         if (lane != 0) return;
         uint32_t it = 0;
         bool ok = true;
         const uint32_t bytes = (uint32_t)(LB5_W * (LB5_TH + 4) * sizeof(T));
-        for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
-            const int tile = u % p.ntx, j0 = (u / p.ntx) * LB5_TH;
-            const int sets = unit_sets5(p, tile, j0);
-            for (int s = 0; s < 2 && ok; ++s) {
-                if (!(sets & (1 << s))) continue;
-                const int q = p.set[s].q;
-                for (int a = 0; a < q && ok; ++a, ++it) {
-                    const int slot = it % LB5_STAGES;
-                    if (it >= LB5_STAGES) ok = mbar_wait(&empty[slot], ((it / LB5_STAGES) - 1) & 1u, P.err, 2);
-                    if (!ok) break;
+        for (;;) {
+            const unsigned k = atomicAdd(P.queue, 1u);
+            const int u = k < (unsigned)P.nunits ? (int)k : -1;
+            const int4 un = u >= 0 ? P.units[u] : make_int4(0, 0, 0, 0);
+            const int q = u >= 0 ? p.set[un.w].q : 1;
+            for (int a = 0; a < q && ok; ++a, ++it) {
+                const int slot = it % LB5_STAGES;
+                if (it >= LB5_STAGES) ok = mbar_wait(&empty[slot], ((it / LB5_STAGES) - 1) & 1u, P.err, 2);
+                if (!ok) break;
+                head[slot] = u;
+                if (u < 0) {
+                    mbar_arrive(&full[slot]);   /* end marker: nothing to copy */
+                } else {
                     mbar_arrive_expect_tx(&full[slot], bytes);
                     /* storage row j0 is node row j0 - 2: the unit's rows and two halo rows each side */
-                    tma_load_3d(smem + (size_t)slot * SLOTB, &P.map[s], &full[slot], tile * LB_TILE_X, j0, a);
+                    tma_load_3d(smem + (size_t)slot * SLOTB, &P.map[un.w], &full[slot], un.x * LB_TILE_X, un.y, a);
                 }
             }
+            if (u < 0 || !ok) break;
         }
         if (!ok) {
             const uint32_t first = it > LB5_STAGES ? it - LB5_STAGES : 0;
@@ -314,31 +500,28 @@ __global__ void __launch_bounds__(32 * (LB5_NC + 1), 1) stream_kernel(const __gr
         return;
     }
 
-    /* consumers */
+    /* consumers: the unit of the next slot is in its header */
     uint32_t it = 0;
     bool alive = true;
-    for (int u = blockIdx.x; u < P.nunits && alive; u += gridDim.x) {
-        const int tile = u % p.ntx, j0 = (u / p.ntx) * LB5_TH;
-        const int sets = unit_sets5(p, tile, j0);
-#pragma unroll 1
-        for (int s = 0; s < 2; ++s) {
-            if (!(sets & (1 << s))) continue;
-            const int q = p.set[s].q;
-            if (q == 9) stream_set<ST, 9, FORCE>(P, s, tile, j0, smem, full, empty, it, alive, pc[s], mc[s]);
-            else if (q == 16) stream_set<ST, 16, FORCE>(P, s, tile, j0, smem, full, empty, it, alive, pc[s], mc[s]);
-            else stream_set<ST, 36, FORCE>(P, s, tile, j0, smem, full, empty, it, alive, pc[s], mc[s]);
-        }
+    while (alive) {
+        const int slot = it % LB5_STAGES;
+        alive = mbar_wait(&full[slot], (it / LB5_STAGES) & 1u, P.err, 1);
+        if (!alive) break;
+        const int u = *(volatile int *)&head[slot];
+        if (u < 0) break;
+        const int4 un = P.units[u];
+        const int q = p.set[un.w].q;
+        if (q == 9) stream_set<ST, 9, FORCE>(P, un.w, un.x, un.y, un.z, smem, full, empty, it, alive, pc[un.w], mc[un.w], hc[un.w]);
+        else if (q == 16)
+            stream_set<ST, 16, FORCE>(P, un.w, un.x, un.y, un.z, smem, full, empty, it, alive, pc[un.w], mc[un.w], hc[un.w]);
+        else stream_set<ST, 36, FORCE>(P, un.w, un.x, un.y, un.z, smem, full, empty, it, alive, pc[un.w], mc[un.w], hc[un.w]);
     }
 }
 
-template <int ST>
-static size_t smem_bytes5()
-{
-    return (size_t)LB5_STAGES * slot_bytes5<ST>() + 2 * LB5_STAGES * sizeof(uint64_t);
-}
 
 template <int ST, bool FORCE>
-static int launch5(const StepParams<typename Store<ST>::R> &p, const TmaMaps &maps, int *err, void *stream)
+static int launch5(const StepParams<typename Store<ST>::R> &p, const TmaMaps &maps, const int4 *units, int nunits,
+                   unsigned int *queue, int *err, void *stream)
 {
     static int configured = 0, nsm = 0;
     const size_t sm = smem_bytes5<ST>();
@@ -353,27 +536,37 @@ static int launch5(const StepParams<typename Store<ST>::R> &p, const TmaMaps &ma
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         configured = 1;
     }
+    if (nunits < 1) return 0;
     Stream5Params<ST> P;
     P.p = p;
     P.err = err;
-    P.nunits = p.ntx * ((p.ny + LB5_TH - 1) / LB5_TH);
+    P.units = units;
+    P.nunits = nunits;
+    P.queue = queue;
     for (int s = 0; s < 2; ++s) P.map[s] = maps.box5[s];
     int grid = nsm;
-    if (grid > P.nunits) grid = P.nunits;
+    if (grid > nunits) grid = nunits;
+    if (cudaMemsetAsync(queue, 0, sizeof(unsigned int), static_cast<cudaStream_t>(stream)) != cudaSuccess) return -1;
     stream_kernel<ST, FORCE><<<grid, 32 * (LB5_NC + 1), sm, static_cast<cudaStream_t>(stream)>>>(P);
     return 0;
 }
 
-int launch_stream(int store, const StepParams<float> &p, const TmaMaps &maps, int *err, void *stream)
+int launch_stream(int store, const StepParams<float> &p, const TmaMaps &maps, const int4 *units, int nunits,
+                  unsigned int *queue, int *err, void *stream)
 {
     const bool f = p.has_force != 0;
+#define LB5_CASE(ST)                                                                        \
+    case ST:                                                                                \
+        return f ? launch5<ST, true>(p, maps, units, nunits, queue, err, stream)            \
+                 : launch5<ST, false>(p, maps, units, nunits, queue, err, stream)
     switch (store) {
-        case 1: return f ? launch5<1, true>(p, maps, err, stream) : launch5<1, false>(p, maps, err, stream);
-        case 2: return f ? launch5<2, true>(p, maps, err, stream) : launch5<2, false>(p, maps, err, stream);
-        case 3: return f ? launch5<3, true>(p, maps, err, stream) : launch5<3, false>(p, maps, err, stream);
-        case 4: return f ? launch5<4, true>(p, maps, err, stream) : launch5<4, false>(p, maps, err, stream);
+        LB5_CASE(1);
+        LB5_CASE(2);
+        LB5_CASE(3);
+        LB5_CASE(4);
         default: return -1;
     }
+#undef LB5_CASE
 }
 
 int stream_rows() { return LB5_TH; }

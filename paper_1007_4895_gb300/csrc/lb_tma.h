@@ -22,8 +22,11 @@ int step3_rows();
 int step3_cols();
 int step3_planes();
 /* Streamed layout (4): TMA-fed single-pass kernel on carried moments (the boundary
- * post-passes follow it). FP32 / FP16 / BF16 storage. 0 on launch, -1 if unavailable. */
-int launch_stream(int store, const StepParams<float> &p, const TmaMaps &maps, int *err, void *stream);
+ * post-passes follow it). FP32 / FP16 / BF16 storage. units: (tile, first row, rows,
+ * set) runs of one set, at most stream_rows() rows, most work first; queue: a device
+ * counter (reset by the launch). 0 on launch, -1 if unavailable. */
+int launch_stream(int store, const StepParams<float> &p, const TmaMaps &maps, const int4 *units, int nunits,
+                  unsigned int *queue, int *err, void *stream);
 int stream_rows();   /* rows per work unit */
 int stream_cols();   /* columns per plane tile: 128 + 2 x 4 ghost */
 }  // namespace lbk

@@ -79,7 +79,10 @@ def test_full_sweep_of_512_channels():
     """All 512 seeded channels, 5000 steps each in graph-captured persistent launches:
     every field finite, and three sampled channels (smallest, largest, a middle one)
     against the FP64 oracle. (Total mass is not an invariant here: the diffuse wall
-    zeroes the normal mass flux at the wall node, not the ghost-node exchange.)"""
+    zeroes the normal mass flux at the wall node, not the ghost-node exchange.)
+    Tolerance: FP32 storage rounds each stored deviation by up to 2^-24 relative per
+    step; over N = 5000 steps these errors add like a random walk, sqrt(N) 2^-24 = 4.2e-6
+    of the velocity scale, so e_u < 5e-6."""
     import paper_1007_4895_gb300 as lb
     import oracle
     from gpu_pair import N1D, field_errors
@@ -100,4 +103,4 @@ def test_full_sweep_of_512_channels():
         o.init_equilibrium(w.rho0, 0.0, 0.0)
         o.step(5000)
         e = field_errors(lat.moments(), o.moments())
-        assert e["u"] < 3e-6 and e["rho"] < 1e-6, (i, w.ny, e)
+        assert e["u"] < 5e-6 and e["rho"] < 1e-6, (i, w.ny, e)
