@@ -32,9 +32,15 @@ namespace lbk {
 
 #define LB_BX 32
 #define LB_BY 8
-#ifndef LB_MINB
-#define LB_MINB 3   /* resident blocks per SM the register budget is sized for */
-#endif
+/* The one-quad kernel per storage format: the resident blocks per SM its register budget
+ * is sized for, and whether it loads population a+1's stencil while computing population
+ * a. Chosen by measurement: with FP32 values the prefetch pays at 128 registers (two
+ * blocks per SM); with 16-bit values the kernel runs faster at 80 registers (three
+ * blocks) without it. */
+template <int ST>
+__host__ __device__ constexpr int step_min_blocks() { return (ST == 3 || ST == 4) ? 3 : 2; }
+template <int ST>
+__host__ __device__ constexpr bool step_prefetch() { return ST == 1 || ST == 2; }
 
 /* Flux difference F_{k+1/2} - F_{k-1/2} along one axis for four nodes in a row
  * (Sec. 3.1), Courant number c, limiter factor kf = (1 - |c|) / 2.
@@ -405,7 +411,7 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
 }
 
 template <int ST>
-__global__ void __launch_bounds__(LB_BX *LB_BY, ST == 0 ? 2 : LB_MINB) step_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p)
+__global__ void __launch_bounds__(LB_BX *LB_BY, step_min_blocks<ST>()) step_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p)
 {
     using R = typename Store<ST>::R;
     __shared__ PopC<R> pc[2][LB_QMAX];
@@ -419,9 +425,10 @@ __global__ void __launch_bounds__(LB_BX *LB_BY, ST == 0 ? 2 : LB_MINB) step_kern
     if (flags & LB_TILE_IFACE) return;   /* mode A interface rows: set by iface_kernel */
     const int s = flags & LB_TILE_HIGH;
     const int q = p.set[s].q;
-    if (q == 9) step_cells<ST, 9>(p, s, flags, x0, j, pc[s], mc[s]);
-    else if (q == 16) step_cells<ST, 16>(p, s, flags, x0, j, pc[s], mc[s]);
-    else step_cells<ST, 36>(p, s, flags, x0, j, pc[s], mc[s]);
+    constexpr bool PF = step_prefetch<ST>();
+    if (q == 9) step_cells<ST, 9, PF>(p, s, flags, x0, j, pc[s], mc[s]);
+    else if (q == 16) step_cells<ST, 16, PF>(p, s, flags, x0, j, pc[s], mc[s]);
+    else step_cells<ST, 36, PF>(p, s, flags, x0, j, pc[s], mc[s]);
 }
 
 
