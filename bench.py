@@ -54,6 +54,9 @@ def workloads():
     return [config2(kn) for kn in KN_SWEEP]
 
 
+ALU_OPS_PER_POP = 45   # FP32 operations per population update (Sec. 3.1 scheme)
+
+
 def algorithmic_bytes(eff_map, sets, store):
     q = np.where(eff_map == 1, sets[1], sets[0])
     return 2 * STORE_BYTES[store] * int(q.sum())
@@ -298,6 +301,18 @@ def main():
                 traffic = tj.get("bytes_per_launch")
         except Exception:
             traffic = None
+    # the same launches against the FP32 ALU: 45 operations per population update (moments
+    # 3, equilibrium and force 8, four limited fluxes 28, update 6), peak = SMs x 128 FP32
+    # lanes x the SM clock sampled during the timed region
+    pops = [algorithmic_bytes(e, lat.sets, args.store) // (2 * STORE_BYTES[args.store]) for e, lat in zip(eff, lats)]
+    avg_pops = statistics.mean(pops[i] for i, _, _ in kt)
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+    alu_peak = nsm * 128 * sm_mhz * 1e6 / 1e9
+    alu_achieved = ALU_OPS_PER_POP * avg_pops / (avg_ms / 1e3) / 1e9
+    roofline_alu = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Gop/s",
+                    "frac": alu_achieved / alu_peak, "ops_per_population": ALU_OPS_PER_POP,
+                    "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (sampled)"}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "lbk::step kernel (one launch per channel per step)",
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, copy burst)",
@@ -352,6 +367,7 @@ def main():
                    "l2": "inputs larger than L2 (156 MB of populations touched per step)",
                    "kernel_variants": variants},
         "roofline": roofline,
+        "roofline_alu": roofline_alu,
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": args.steps * sum(launches_per_step(v) for v in variants),
