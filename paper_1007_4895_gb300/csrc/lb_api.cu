@@ -98,6 +98,11 @@ struct lb_ctx {
     int4 *d_units = nullptr;
     size_t units_cap = 0;
     unsigned int *d_squeue = nullptr;
+    /* one-quad kernel: block launch order, most work first */
+    std::vector<int> border_h;
+    int *d_border = nullptr;
+    size_t border_cap = 0;
+    bool border_used = false;       /* false: the order is the raster order */
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     /* learned placement */
     lb_mlp *mlp = nullptr;
@@ -196,6 +201,7 @@ StepParams<R> make_params(const lb_ctx *c, int in, int out, double t_new)
     p.sr = (c->opts.rounding == LB_ROUND_STOCHASTIC &&
             (c->store == LB_STORE_F16_DEV || c->store == LB_STORE_BF16_DEV)) ? 1 : 0;
     p.step_key = (uint32_t)(c->step + (in != out ? 1 : 0));
+    p.block_order = nullptr;   /* layout 5 sets it */
     p.aux_in = c->aux[in];
     p.aux_out = c->aux[out];
     p.rho0 = R(c->opts.rho0);
@@ -369,6 +375,41 @@ int build_edge_lists(lb_ctx *c)
                                                   c->stream), "edge list upload"))
             return e;
     }
+    /* launch order of the one-quad kernel's blocks for layout 5 (one tile x LB_STEP_BY
+     * rows): blocks with a high-order row first, so that the long blocks are all in the
+     * first wave, raster order within each group. Few waves: the tail shrinks; many
+     * waves over a lattice larger than L2: the raster order, which mixes long and short
+     * blocks, can be faster. The autotuner decides; layout 5 is not offered when the
+     * order is the raster order. */
+    {
+        const int nby = (c->ny + LB_STEP_BY - 1) / LB_STEP_BY;
+        std::vector<int> &B = c->border_h;
+        std::vector<int> key((size_t)nby * c->ntx);
+        B.resize(key.size());
+        for (int by = 0; by < nby; ++by)
+            for (int tx = 0; tx < c->ntx; ++tx) {
+                int qmax = 0;
+                for (int j = by * LB_STEP_BY; j < std::min(c->ny, (by + 1) * LB_STEP_BY); ++j) {
+                    const uint8_t f = c->tmap[(size_t)j * c->ntx + tx];
+                    if (!(f & LB_TILE_IFACE)) qmax = std::max(qmax, c->q[f & LB_TILE_HIGH]);
+                }
+                const int b = by * c->ntx + tx;
+                B[b] = b;
+                key[b] = qmax;
+            }
+        std::stable_sort(B.begin(), B.end(), [&](int a, int b) { return key[a] > key[b]; });
+        c->border_used = false;
+        for (size_t k = 0; k < B.size() && !c->border_used; ++k) c->border_used = B[k] != (int)k;
+        if (B.size() > c->border_cap) {
+            int *d = static_cast<int *>(own(c, B.size() * sizeof(int)));
+            if (!d) return fail(LB_ERR_NOMEM, "device allocation failed");
+            c->d_border = d;
+            c->border_cap = B.size();
+        }
+        if (int e = cuda_check(c, cudaMemcpyAsync(c->d_border, B.data(), B.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                                  c->stream), "block order upload"))
+            return e;
+    }
     /* work units of the streamed layout: runs of one set in a tile column, at most
      * stream_rows() rows each, most work (populations x rows) first */
     std::vector<int4> &U = c->units_h;
@@ -413,7 +454,8 @@ int upload_tiles(lb_ctx *c)
 /* variant 0: one node quad per thread (lb_step_impl.cuh); 1: TMA-fed producer /
  * consumer blocks (lb_step3.cu, not for FP64 storage); 2, 3: split step, plain kernel
  * on 4 x 1 or 4 x 2 register blocks plus the one-quad kernel on the edge list
- * (lb_step_impl.cuh). */
+ * (lb_step_impl.cuh); 4: streamed (lb_stream.cu); 5: variant 0 with the blocks that
+ * hold high-order rows launched first. */
 template <typename R>
 void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
 {
@@ -442,6 +484,12 @@ void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
         }
         return;
     }
+    if (variant == 5 && c->border_used) {
+        StepParams<R> q = p;
+        q.block_order = c->d_border;
+        lbk::launch_step<R>(c->store, q, c->stream);
+        return;
+    }
     lbk::launch_step<R>(c->store, p, c->stream);
 }
 
@@ -451,6 +499,7 @@ bool variant_available(const lb_ctx *c, int v)
     if (v == 1) return c->tma_ok;
     if (v == 2 || v == 3) return c->edge_stream != nullptr;
     if (v == 4) return c->tma_ok && c->opts.iface == LB_IFACE_HERMITE;
+    if (v == 5) return c->border_used;
     return v >= 0 && v < LB_NUM_VARIANTS;
 }
 

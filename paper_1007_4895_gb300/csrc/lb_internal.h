@@ -27,6 +27,7 @@
 #define LB_TILE_X 128
 #define LB_QMAX 36
 #define LB_MAX_IFACE 64
+#define LB_STEP_BY 8    /* rows per block of the one-quad kernel (its blocks are one tile wide) */
 
 enum : uint8_t {
     LB_TILE_HIGH = 1u,     /* tile uses set 1 */
@@ -61,6 +62,10 @@ struct StepParams {
      * of the level read (aux_in) and of the level written (aux_out) */
     const void *aux_in;
     void *aux_out;
+    /* one-quad kernel: launch order of its blocks (tile + ntx * band of LB_STEP_BY rows),
+     * blocks with a high-order row first, so that the long blocks start in the first
+     * wave; NULL: the natural two-dimensional grid */
+    const int *block_order;
     int sr;                         /* stochastic rounding of the updated populations */
     uint32_t step_key;              /* the step being computed (random-bit key) */
     R rho0, dt;
@@ -111,8 +116,9 @@ template <typename R>
 void launch_aux(int store, const StepParams<R> &p, const int2 *list, int n, void *stream);
 /* step-kernel layouts: 0 one node quad per thread, 1 TMA-fed producer / consumer,
  * 2 and 3 split plain / edge kernels with register blocks of 4 x 1 and 4 x 2 nodes,
- * 4 streamed (TMA, carried moments, boundary post-passes) */
-#define LB_NUM_VARIANTS 5
+ * 4 streamed (TMA, carried moments, boundary work at the end of each unit), 5 layout 0
+ * with its blocks launched in block_order */
+#define LB_NUM_VARIANTS 6
 
 /* The quad of nodes x0 .. x0+3 of row j needs none of the boundary work of the step
  * (wall overwrite, ghost-row or ghost-column copies, pressure column, mode-B shadow or

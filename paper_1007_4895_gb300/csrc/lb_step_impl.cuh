@@ -31,7 +31,7 @@
 namespace lbk {
 
 #define LB_BX 32
-#define LB_BY 8
+#define LB_BY LB_STEP_BY
 /* The one-quad kernel per storage format: the resident blocks per SM its register budget
  * is sized for, and whether it loads population a+1's stencil while computing population
  * a. Chosen by measurement: with FP32 values the prefetch pays at 128 registers (two
@@ -418,8 +418,14 @@ __global__ void __launch_bounds__(LB_BX *LB_BY, step_min_blocks<ST>()) step_kern
     __shared__ MomC<R> mc[2][LB_QMAX];
     stage_consts(p, pc, mc, threadIdx.y * LB_BX + threadIdx.x, LB_BX * LB_BY);
     __syncthreads();
-    const int j = blockIdx.y * LB_BY + threadIdx.y;
-    const int x0 = (blockIdx.x * LB_BX + threadIdx.x) * 4;
+    int bx = blockIdx.x, by = blockIdx.y;
+    if (p.block_order) {
+        const int b = p.block_order[blockIdx.x];
+        bx = b % p.ntx;
+        by = b / p.ntx;
+    }
+    const int j = by * LB_BY + threadIdx.y;
+    const int x0 = (bx * LB_BX + threadIdx.x) * 4;
     if (j >= p.ny || x0 >= p.nx) return;
     const uint8_t flags = p.tmap[(size_t)j * p.ntx + (x0 / LB_TILE_X)];
     if (flags & LB_TILE_IFACE) return;   /* mode A interface rows: set by iface_kernel */
@@ -783,8 +789,10 @@ int batch_blocks_per_sm(int threads)
 template <int ST>
 void launch_step_store(const StepParams<typename Store<ST>::R> &p, void *stream)
 {
+    static_assert(4 * LB_BX == LB_TILE_X, "a block of the one-quad kernel is one tile wide");
     dim3 block(LB_BX, LB_BY);
     dim3 grid((p.nx + 4 * LB_BX - 1) / (4 * LB_BX), (p.ny + LB_BY - 1) / LB_BY);
+    if (p.block_order) grid = dim3(grid.x * grid.y, 1);
     step_kernel<ST><<<grid, block, 0, static_cast<cudaStream_t>(stream)>>>(p);
 }
 
