@@ -103,6 +103,10 @@ struct lb_ctx {
     int *d_border = nullptr;
     size_t border_cap = 0;
     bool border_used = false;       /* false: the order is the raster order */
+    std::vector<int2> bdesc_h;      /* layout 6 block descriptors */
+    int2 *d_bdesc = nullptr;
+    size_t bdesc_cap = 0;
+    bool bdesc_narrow = false;      /* some band runs two nodes per thread */
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     /* learned placement */
     lb_mlp *mlp = nullptr;
@@ -202,6 +206,7 @@ StepParams<R> make_params(const lb_ctx *c, int in, int out, double t_new)
             (c->store == LB_STORE_F16_DEV || c->store == LB_STORE_BF16_DEV)) ? 1 : 0;
     p.step_key = (uint32_t)(c->step + (in != out ? 1 : 0));
     p.block_order = nullptr;   /* layout 5 sets it */
+    p.block_desc = nullptr;    /* layout 6 sets it */
     p.aux_in = c->aux[in];
     p.aux_out = c->aux[out];
     p.rho0 = R(c->opts.rho0);
@@ -410,6 +415,40 @@ int build_edge_lists(lb_ctx *c)
                                                   c->stream), "block order upload"))
             return e;
     }
+    /* layout 6: a band of LB_STEP_BY rows holding a row of a set with 16 or more
+     * populations runs as two blocks of 4 rows with two nodes per thread; these come
+     * first, then the other bands, raster order within each group */
+    {
+        const int nby = (c->ny + LB_STEP_BY - 1) / LB_STEP_BY;
+        std::vector<int2> &D = c->bdesc_h;
+        std::vector<int2> wide;
+        D.clear();
+        for (int by = 0; by < nby; ++by)
+            for (int tx = 0; tx < c->ntx; ++tx) {
+                bool high = false;
+                for (int j = by * LB_STEP_BY; j < std::min(c->ny, (by + 1) * LB_STEP_BY); ++j) {
+                    const uint8_t f = c->tmap[(size_t)j * c->ntx + tx];
+                    if (!(f & LB_TILE_IFACE) && c->q[f & LB_TILE_HIGH] >= 16) high = true;
+                }
+                const int j0 = by * LB_STEP_BY;
+                if (high) {
+                    for (int h = 0; h < LB_STEP_BY && j0 + h < c->ny; h += 4) D.push_back(make_int2(tx, 2 * (j0 + h) + 1));
+                } else {
+                    wide.push_back(make_int2(tx, 2 * j0));
+                }
+            }
+        c->bdesc_narrow = !D.empty();
+        D.insert(D.end(), wide.begin(), wide.end());
+        if (D.size() > c->bdesc_cap) {
+            int2 *d = static_cast<int2 *>(own(c, D.size() * sizeof(int2)));
+            if (!d) return fail(LB_ERR_NOMEM, "device allocation failed");
+            c->d_bdesc = d;
+            c->bdesc_cap = D.size();
+        }
+        if (int e = cuda_check(c, cudaMemcpyAsync(c->d_bdesc, D.data(), D.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                                  c->stream), "block descriptor upload"))
+            return e;
+    }
     /* work units of the streamed layout: runs of one set in a tile column, at most
      * stream_rows() rows each, most work (populations x rows) first */
     std::vector<int4> &U = c->units_h;
@@ -455,7 +494,8 @@ int upload_tiles(lb_ctx *c)
  * consumer blocks (lb_step3.cu, not for FP64 storage); 2, 3: split step, plain kernel
  * on 4 x 1 or 4 x 2 register blocks plus the one-quad kernel on the edge list
  * (lb_step_impl.cuh); 4: streamed (lb_stream.cu); 5: variant 0 with the blocks that
- * hold high-order rows launched first. */
+ * hold high-order rows launched first; 6: as 5, with two nodes per thread in the bands
+ * that hold high-order rows. */
 template <typename R>
 void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
 {
@@ -484,6 +524,12 @@ void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
         }
         return;
     }
+    if (variant == 6 && c->bdesc_narrow) {
+        StepParams<R> q = p;
+        q.block_desc = c->d_bdesc;
+        lbk::launch_step_desc<R>(c->store, q, (int)c->bdesc_h.size(), c->stream);
+        return;
+    }
     if (variant == 5 && c->border_used) {
         StepParams<R> q = p;
         q.block_order = c->d_border;
@@ -500,6 +546,7 @@ bool variant_available(const lb_ctx *c, int v)
     if (v == 2 || v == 3) return c->edge_stream != nullptr;
     if (v == 4) return c->tma_ok && c->opts.iface == LB_IFACE_HERMITE;
     if (v == 5) return c->border_used;
+    if (v == 6) return c->bdesc_narrow;
     return v >= 0 && v < LB_NUM_VARIANTS;
 }
 

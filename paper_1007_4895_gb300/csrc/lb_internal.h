@@ -66,6 +66,10 @@ struct StepParams {
      * blocks with a high-order row first, so that the long blocks start in the first
      * wave; NULL: the natural two-dimensional grid */
     const int *block_order;
+    /* layout 6: block descriptors (tile, 2 * first row + h); h = 1: 4 rows, two nodes
+     * per thread (bands holding high-order rows), h = 0: LB_STEP_BY rows, one quad per
+     * thread */
+    const int2 *block_desc;
     int sr;                         /* stochastic rounding of the updated populations */
     uint32_t step_key;              /* the step being computed (random-bit key) */
     R rho0, dt;
@@ -94,6 +98,9 @@ namespace lbk {
  * 1 = TMA-fed producer / consumer blocks (lb_step3.cu, FP32 / FP16 / BF16 storage) */
 template <typename R>
 void launch_step(int store, const StepParams<R> &p, void *stream);
+/* layout 6: the one-quad kernel over n block descriptors (p.block_desc) */
+template <typename R>
+void launch_step_desc(int store, const StepParams<R> &p, int n, void *stream);
 /* Split form of the step: a plain kernel over the quads for which plain_quad() holds,
  * in register blocks of 4 x rb nodes (rb = 1 or 2; a block is plain when all its rb
  * quads are), and the one-quad kernel over the listed remaining quads (x0, j) on
@@ -117,8 +124,9 @@ void launch_aux(int store, const StepParams<R> &p, const int2 *list, int n, void
 /* step-kernel layouts: 0 one node quad per thread, 1 TMA-fed producer / consumer,
  * 2 and 3 split plain / edge kernels with register blocks of 4 x 1 and 4 x 2 nodes,
  * 4 streamed (TMA, carried moments, boundary work at the end of each unit), 5 layout 0
- * with its blocks launched in block_order */
-#define LB_NUM_VARIANTS 6
+ * with its blocks launched in block_order, 6 the same kernel on block_desc (two nodes
+ * per thread in high-order bands) */
+#define LB_NUM_VARIANTS 7
 
 /* The quad of nodes x0 .. x0+3 of row j needs none of the boundary work of the step
  * (wall overwrite, ghost-row or ghost-column copies, pressure column, mode-B shadow or

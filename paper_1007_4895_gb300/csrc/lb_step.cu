@@ -14,6 +14,8 @@ namespace lbk {
 template <int ST>
 void launch_step_store(const StepParams<typename Store<ST>::R> &p, void *stream);
 template <int ST>
+void launch_step_desc_store(const StepParams<typename Store<ST>::R> &p, int n, void *stream);
+template <int ST>
 void launch_step_split_store(const StepParams<typename Store<ST>::R> &p, int rb, const int2 *edge, int n_edge,
                              void *stream, void *edge_stream);
 
@@ -280,6 +282,12 @@ void launch_step(int store, const StepParams<R> &p, void *stream)
     LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) launch_step_store<ST>(p, stream));
 }
 
+template <typename R>
+void launch_step_desc(int store, const StepParams<R> &p, int n, void *stream)
+{
+    LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) launch_step_desc_store<ST>(p, n, stream));
+}
+
 template <int ST>
 int launch_batch_store(const void *params, const int *order, int n, int nsteps, int base, int advance,
                        unsigned int *queue, int threads, int grid, void *stream);
@@ -337,6 +345,8 @@ void launch_shadows(int store, const StepParams<R> &p, void *stream)
 
 template void launch_step<float>(int, const StepParams<float> &, void *);
 template void launch_step<double>(int, const StepParams<double> &, void *);
+template void launch_step_desc<float>(int, const StepParams<float> &, int, void *);
+template void launch_step_desc<double>(int, const StepParams<double> &, int, void *);
 template void launch_step_split<float>(int, const StepParams<float> &, int, const int2 *, int, void *, void *);
 template void launch_step_split<double>(int, const StepParams<double> &, int, const int2 *, int, void *, void *);
 template void launch_iface<float>(int, const StepParams<float> &, void *);

@@ -42,61 +42,61 @@ __host__ __device__ constexpr int step_min_blocks() { return (ST == 3 || ST == 4
 template <int ST>
 __host__ __device__ constexpr bool step_prefetch() { return ST == 1 || ST == 2; }
 
-/* Flux difference F_{k+1/2} - F_{k-1/2} along one axis for four nodes in a row
- * (Sec. 3.1), Courant number c, limiter factor kf = (1 - |c|) / 2.
- * v[-2..5] are the values at nodes x0-2 .. x0+5 (v[0..3] the thread's own). */
-template <typename R>
-__device__ __forceinline__ void x_flux_diff(R c, R kf, const R l[2], const R v[4], const R r[2], R D[4])
+/* Flux difference F_{k+1/2} - F_{k-1/2} along one axis for NQ (2 or 4) nodes in a row
+ * (Sec. 3.1), Courant number c, limiter factor kf = (1 - |c|) / 2. l[0..1] are the
+ * values at nodes x0-2, x0-1, v[0..NQ-1] the thread's own, r[0..1] those at x0+NQ,
+ * x0+NQ+1. A node's result depends only on its own neighbourhood, so it is the same
+ * for either NQ. */
+template <int NQ = 4, typename R>
+__device__ __forceinline__ void x_flux_diff(R c, R kf, const R l[2], const R v[NQ], const R r[2], R D[NQ])
 {
     if (c > R(0)) {
         /* upwind node k: F_{k+1/2} = f_k + kf minmod(f_k - f_{k-1}, f_{k+1} - f_k) */
-        R d[6];
+        R d[NQ + 2];
         d[0] = l[1] - l[0];
         d[1] = v[0] - l[1];
-        d[2] = v[1] - v[0];
-        d[3] = v[2] - v[1];
-        d[4] = v[3] - v[2];
-        d[5] = r[0] - v[3];
-        R n[6], m[5];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) n[k] = neg_part(d[k]);
+        for (int k = 1; k < NQ; ++k) d[k + 1] = v[k] - v[k - 1];
+        d[NQ + 1] = r[0] - v[NQ - 1];
+        R n[NQ + 2], m[NQ + 1];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) m[k] = minmod_n(d[k], d[k + 1], n[k], n[k + 1]);
+        for (int k = 0; k < NQ + 2; ++k) n[k] = neg_part(d[k]);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) D[k] = fma(kf, m[k + 1] - m[k], d[k + 1]);
+        for (int k = 0; k < NQ + 1; ++k) m[k] = minmod_n(d[k], d[k + 1], n[k], n[k + 1]);
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) D[k] = fma(kf, m[k + 1] - m[k], d[k + 1]);
     } else if (c < R(0)) {
         /* mirror image: upwind node k+1 */
-        R e[6];
+        R e[NQ + 2];
         e[0] = v[0] - l[1];
-        e[1] = v[1] - v[0];
-        e[2] = v[2] - v[1];
-        e[3] = v[3] - v[2];
-        e[4] = r[0] - v[3];
-        e[5] = r[1] - r[0];
-        R n[6], m[5];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) n[k] = neg_part(e[k]);
+        for (int k = 1; k < NQ; ++k) e[k] = v[k] - v[k - 1];
+        e[NQ] = r[0] - v[NQ - 1];
+        e[NQ + 1] = r[1] - r[0];
+        R n[NQ + 2], m[NQ + 1];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) m[k] = minmod_n(e[k], e[k + 1], n[k], n[k + 1]);
+        for (int k = 0; k < NQ + 2; ++k) n[k] = neg_part(e[k]);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) D[k] = fma(-kf, m[k + 1] - m[k], e[k + 1]);
+        for (int k = 0; k < NQ + 1; ++k) m[k] = minmod_n(e[k], e[k + 1], n[k], n[k + 1]);
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) D[k] = fma(-kf, m[k + 1] - m[k], e[k + 1]);
     } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) D[k] = R(0);
+        for (int k = 0; k < NQ; ++k) D[k] = R(0);
     }
 }
 
 /* Stored values one population needs for a quad: its own four, two beside them on each
  * side (x flux, when xi_x != 0) and three rows on the upwind / downwind sides (y flux,
  * when xi_y != 0: rows j-2, j-1, j+1 for xi_y > 0, rows j-1, j+1, j+2 for xi_y < 0). */
-template <typename T>
+template <typename T, int NQ = 4>
 struct QuadStencil {
-    T v[4], l[2], r[2], y0[4], y1[4], y2[4];
+    T v[NQ], l[2], r[2], y0[NQ], y1[NQ], y2[NQ];
 };
 
 /* PF: load population a + 1 while population a is computed (one-deep software
  * pipeline), for kernels whose threads are few and latency-bound. */
-template <int ST, int Q, bool PF = false>
+template <int ST, int Q, bool PF = false, int NQ = 4>
 __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::R> &p, int s, uint8_t flags, int x0,
                                            int j, const PopC<typename Store<ST>::R> *pcs,
                                            const MomC<typename Store<ST>::R> *mcs)
@@ -115,14 +115,16 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
     const R rho0 = p.rho0;
 
     /* 1. moments */
-    R rhod[4] = {R(0), R(0), R(0), R(0)}, jx[4] = {R(0), R(0), R(0), R(0)}, jy[4] = {R(0), R(0), R(0), R(0)};
+    R rhod[NQ], jx[NQ], jy[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) rhod[k] = jx[k] = jy[k] = R(0);
 #pragma unroll 4
     for (int a = 0; a < Q; ++a) {
-        T raw[4];
-        ld4(fin + a * plane + row0, raw);
+        T raw[NQ];
+        ldn<NQ>(fin + a * plane + row0, raw);
         const MomC<R> mc = mcs[a];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < NQ; ++k) {
             R d = decode<ST>(raw[k], mc.winv, rho0);
             rhod[k] = fma(mc.w, d, rhod[k]);
             jx[k] = fma(mc.wcx, d, jx[k]);
@@ -130,9 +132,9 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
         }
     }
     /* 2. macroscopic state and relaxation */
-    R rho[4], ux[4], uy[4], usq[4], om[4], gu[4];
+    R rho[NQ], ux[NQ], uy[NQ], usq[NQ], om[NQ], gu[NQ];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < NQ; ++k) {
         rho[k] = rho0 + rhod[k];
         R inv = R(1) / rho[k];
         ux[k] = jx[k] * inv;
@@ -147,72 +149,74 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
     if (j == p.ny - 1 && p.wall_diffuse[1]) wall = 1;
     const R nsgn = wall == 0 ? R(1) : R(-1);
 
-    bool valid[4];
+    bool valid[NQ];
     bool full = true;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < NQ; ++k) {
         int x = x0 + k;
         valid[k] = x < p.nx && !is_pressure_node(p, x, j);
         full = full && valid[k];
     }
-    const bool near_x_edge = p.periodic_x && (x0 < LB_GHOST || x0 + 3 >= p.nx - LB_GHOST);
+    const bool near_x_edge = p.periodic_x && (x0 < LB_GHOST || x0 + NQ - 1 >= p.nx - LB_GHOST);
 
     int img[2];
     const int nimg = row_images(p, j, img);
     /* a >= 0: an updated population (stochastically rounded when p.sr); a < 0: a value
      * set by the wall (rounded to nearest) */
-    auto store_quad = [&](T *dst, const R dn[4], R w, int a) {
-        T e[4];
+    auto store_quad = [&](T *dst, const R dn[NQ], R w, int a) {
+        T e[NQ];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < NQ; ++k)
             e[k] = (a >= 0 && p.sr) ? encode_sr<ST>(dn[k], w, rho0, sr_bits(x0 + k, j, p.nx, a, p.step_key))
                                     : encode<ST>(dn[k], w, rho0);
         for (int t = -1; t < nimg; ++t) {
             T *d = t < 0 ? dst : dst + (ptrdiff_t)img[t] * p.pitch;
             if (full && !near_x_edge) {
-                st4(d, e);
+                stn<NQ>(d, e);
             } else {
                 T *prow = d - (x0 + LB_GHOST);
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
+                for (int k = 0; k < NQ; ++k)
                     if (valid[k]) put1(p, prow, x0 + k, e[k]);
             }
         }
     };
 
     /* 3. stencil, fluxes, collision, force (PF: loads one population ahead) */
-    R num[4] = {R(0), R(0), R(0), R(0)};
+    R num[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) num[k] = R(0);
     if constexpr (!PF) {
     #pragma unroll 1
         for (int a = 0; a < Q; ++a) {
             const T *pa = fin + a * plane + row0;
             const PopC<R> pc = pcs[a];
             const R winv = pc.winv;
-            T raw[4];
-            R v[4], l[2], r[2];
-            ld4(pa, raw);
+            T raw[NQ];
+            R v[NQ], l[2], r[2];
+            ldn<NQ>(pa, raw);
     #pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] = decode<ST>(raw[k], winv, rho0);
-            R Dx[4], Dy[4];
+            for (int k = 0; k < NQ; ++k) v[k] = decode<ST>(raw[k], winv, rho0);
+            R Dx[NQ], Dy[NQ];
             const R crx = pc.crx, cry = pc.cry;
             if (crx != R(0)) {
                 T tl[2], tr[2];
                 ld2(pa - 2, tl);
-                ld2(pa + 4, tr);
+                ld2(pa + NQ, tr);
                 l[0] = decode<ST>(tl[0], winv, rho0);
                 l[1] = decode<ST>(tl[1], winv, rho0);
                 r[0] = decode<ST>(tr[0], winv, rho0);
                 r[1] = decode<ST>(tr[1], winv, rho0);
             }
-            x_flux_diff(crx, pc.kx, l, v, r, Dx);
+            x_flux_diff<NQ>(crx, pc.kx, l, v, r, Dx);
             if (cry > R(0)) {
-                T t2[4], t1[4], tp[4];
-                ld4(pa + om2, t2);
-                ld4(pa + om1, t1);
-                ld4(pa + op1, tp);
+                T t2[NQ], t1[NQ], tp[NQ];
+                ldn<NQ>(pa + om2, t2);
+                ldn<NQ>(pa + om1, t1);
+                ldn<NQ>(pa + op1, tp);
                 const R kf = pc.ky;
     #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < NQ; ++k) {
                     R ym2 = decode<ST>(t2[k], winv, rho0), ym1 = decode<ST>(t1[k], winv, rho0);
                     R yp1 = decode<ST>(tp[k], winv, rho0);
                     R d0 = ym1 - ym2, d1 = v[k] - ym1, d2 = yp1 - v[k];
@@ -220,13 +224,13 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
                     Dy[k] = fma(kf, minmod_n(d1, d2, n1, neg_part(d2)) - minmod_n(d0, d1, neg_part(d0), n1), d1);
                 }
             } else if (cry < R(0)) {
-                T t1[4], tp[4], t2[4];
-                ld4(pa + om1, t1);
-                ld4(pa + op1, tp);
-                ld4(pa + op2, t2);
+                T t1[NQ], tp[NQ], t2[NQ];
+                ldn<NQ>(pa + om1, t1);
+                ldn<NQ>(pa + op1, tp);
+                ldn<NQ>(pa + op2, t2);
                 const R kf = pc.ky;
     #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < NQ; ++k) {
                     R ym1 = decode<ST>(t1[k], winv, rho0), yp1 = decode<ST>(tp[k], winv, rho0);
                     R yp2 = decode<ST>(t2[k], winv, rho0);
                     R e0 = v[k] - ym1, e1 = yp1 - v[k], e2 = yp2 - yp1;
@@ -235,13 +239,13 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
                 }
             } else {
     #pragma unroll
-                for (int k = 0; k < 4; ++k) Dy[k] = R(0);
+                for (int k = 0; k < NQ; ++k) Dy[k] = R(0);
             }
-            R dn[4];
+            R dn[NQ];
             const R cxa = pc.cx, cya = pc.cy;
             const R gxi = xi_dot(cxa, cya, p.gx, p.gy);
     #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < NQ; ++k) {
                 R eu = xi_dot(cxa, cya, ux[k], uy[k]);
                 R de = deq(rhod[k], rho[k], eu, usq[k]);
                 /* sum the small increments first and round onto the stored magnitude once */
@@ -256,32 +260,32 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
                 if (xn > R(0)) continue;   /* replaced below */
                 if (xn < R(0)) {
     #pragma unroll
-                    for (int k = 0; k < 4; ++k) num[k] = fma(-xn * pc.w, dn[k], num[k]);
+                    for (int k = 0; k < NQ; ++k) num[k] = fma(-xn * pc.w, dn[k], num[k]);
                 }
             }
             store_quad(fout + a * plane + row0, dn, pc.w, a);
         }
 
     } else {
-        auto load = [&](int a, QuadStencil<T> &S, PopC<R> &pc) {
+        auto load = [&](int a, QuadStencil<T, NQ> &S, PopC<R> &pc) {
             pc = pcs[a];
             const T *pa = fin + a * plane + row0;
-            ld4(pa, S.v);
+            ldn<NQ>(pa, S.v);
             if (pc.crx != R(0)) {
                 ld2(pa - 2, S.l);
-                ld2(pa + 4, S.r);
+                ld2(pa + NQ, S.r);
             }
             if (pc.cry > R(0)) {
-                ld4(pa + om2, S.y0);
-                ld4(pa + om1, S.y1);
-                ld4(pa + op1, S.y2);
+                ldn<NQ>(pa + om2, S.y0);
+                ldn<NQ>(pa + om1, S.y1);
+                ldn<NQ>(pa + op1, S.y2);
             } else if (pc.cry < R(0)) {
-                ld4(pa + om1, S.y0);
-                ld4(pa + op1, S.y1);
-                ld4(pa + op2, S.y2);
+                ldn<NQ>(pa + om1, S.y0);
+                ldn<NQ>(pa + op1, S.y1);
+                ldn<NQ>(pa + op2, S.y2);
             }
         };
-        QuadStencil<T> cur, nxt;
+        QuadStencil<T, NQ> cur, nxt;
         PopC<R> pcur, pnxt;
         if constexpr (PF) load(0, cur, pcur);
     #pragma unroll 1
@@ -293,10 +297,10 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
             }
             const PopC<R> pc = pcur;
             const R winv = pc.winv;
-            R v[4], l[2], r[2];
+            R v[NQ], l[2], r[2];
     #pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] = decode<ST>(cur.v[k], winv, rho0);
-            R Dx[4], Dy[4];
+            for (int k = 0; k < NQ; ++k) v[k] = decode<ST>(cur.v[k], winv, rho0);
+            R Dx[NQ], Dy[NQ];
             const R crx = pc.crx, cry = pc.cry;
             if (crx != R(0)) {
                 l[0] = decode<ST>(cur.l[0], winv, rho0);
@@ -304,11 +308,11 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
                 r[0] = decode<ST>(cur.r[0], winv, rho0);
                 r[1] = decode<ST>(cur.r[1], winv, rho0);
             }
-            x_flux_diff(crx, pc.kx, l, v, r, Dx);
+            x_flux_diff<NQ>(crx, pc.kx, l, v, r, Dx);
             if (cry > R(0)) {
                 const R kf = pc.ky;
     #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < NQ; ++k) {
                     R ym2 = decode<ST>(cur.y0[k], winv, rho0), ym1 = decode<ST>(cur.y1[k], winv, rho0);
                     R yp1 = decode<ST>(cur.y2[k], winv, rho0);
                     R d0 = ym1 - ym2, d1 = v[k] - ym1, d2 = yp1 - v[k];
@@ -318,7 +322,7 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
             } else if (cry < R(0)) {
                 const R kf = pc.ky;
     #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < NQ; ++k) {
                     R ym1 = decode<ST>(cur.y0[k], winv, rho0), yp1 = decode<ST>(cur.y1[k], winv, rho0);
                     R yp2 = decode<ST>(cur.y2[k], winv, rho0);
                     R e0 = v[k] - ym1, e1 = yp1 - v[k], e2 = yp2 - yp1;
@@ -327,13 +331,13 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
                 }
             } else {
     #pragma unroll
-                for (int k = 0; k < 4; ++k) Dy[k] = R(0);
+                for (int k = 0; k < NQ; ++k) Dy[k] = R(0);
             }
-            R dn[4];
+            R dn[NQ];
             const R cxa = pc.cx, cya = pc.cy;
             const R gxi = xi_dot(cxa, cya, p.gx, p.gy);
     #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < NQ; ++k) {
                 R eu = xi_dot(cxa, cya, ux[k], uy[k]);
                 R de = deq(rhod[k], rho[k], eu, usq[k]);
                 /* sum the small increments first and round onto the stored magnitude once */
@@ -349,7 +353,7 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
                 replaced = xn > R(0);
                 if (xn < R(0)) {
     #pragma unroll
-                    for (int k = 0; k < 4; ++k) num[k] = fma(-xn * pc.w, dn[k], num[k]);
+                    for (int k = 0; k < NQ; ++k) num[k] = fma(-xn * pc.w, dn[k], num[k]);
                 }
             }
             if (!replaced) store_quad(fout + a * plane + row0, dn, pc.w, a);
@@ -366,18 +370,18 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
         const R uwx = p.uw_x[wall], uwy = p.uw_y[wall];
         const R usw = uwx * uwx + uwy * uwy;
         const R kd = p.kdiff[s][wall], kout = p.kout[s][wall];
-        R rwd[4];
+        R rwd[NQ];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) rwd[k] = fma(rho0, kd, num[k]) / kout;   /* rho_W - rho0 */
+        for (int k = 0; k < NQ; ++k) rwd[k] = fma(rho0, kd, num[k]) / kout;   /* rho_W - rho0 */
 #pragma unroll 1
         for (int a = 0; a < Q; ++a) {
             if (c.cy[a] * nsgn <= R(0)) continue;
             const R ew = c.cx[a] * uwx + c.cy[a] * uwy;
             const R sm1 = ew + R(0.5) * (ew * ew - usw);    /* S / w - 1 */
-            R dn[4];
+            R dn[NQ];
             /* rho_W S / w - rho0 = (rho_W - rho0)(1 + sm1) + rho0 sm1 */
 #pragma unroll
-            for (int k = 0; k < 4; ++k) dn[k] = fma(rwd[k] + rho0, sm1, rwd[k]);
+            for (int k = 0; k < NQ; ++k) dn[k] = fma(rwd[k] + rho0, sm1, rwd[k]);
             store_quad(fout + a * plane + row0, dn, c.w[a], -1);
         }
     }
@@ -386,16 +390,16 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
     if (flags & LB_TILE_SHADOW) {
         const int t = 1 - s;
         const SetConst<R> &ct = p.set[t];
-        R h[4][6];
+        R h[NQ][6];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < NQ; ++k)
 #pragma unroll
             for (int m = 0; m < 6; ++m) h[k][m] = R(0);
 #pragma unroll 1
         for (int a = 0; a < Q; ++a) {
             const T *pa = fout + a * plane + row0;
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < NQ; ++k)
                 if (valid[k]) hermite_acc(c, a, decode<ST>(pa[k], c.winv[a], rho0), h[k]);
         }
         T *ftd = static_cast<T *>(p.fout[t]);
@@ -404,7 +408,7 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
         for (int b = 0; b < qt; ++b) {
             T *prow = ftd + b * plane + (size_t)j * p.pitch;
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < NQ; ++k)
                 if (valid[k]) put1r(p, prow, x0 + k, j, encode<ST>(hermite_rebuild(ct, b, h[k]), ct.w[b], rho0));
         }
     }
@@ -784,6 +788,49 @@ int batch_blocks_per_sm(int threads)
         return 0;
     }
     return per_sm;
+}
+
+/* Layout 6: one block per descriptor of p.block_desc, one tile wide. A band that holds
+ * high-order rows runs as blocks of 4 rows with two nodes per thread (64 threads per
+ * row), so its long population loops are spread over twice the warps; the other bands
+ * run as in step_kernel. Each node's arithmetic is the same for either width. */
+template <int ST>
+__global__ void __launch_bounds__(LB_BX *LB_BY, step_min_blocks<ST>())
+    step_desc_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p)
+{
+    using R = typename Store<ST>::R;
+    __shared__ PopC<R> pc[2][LB_QMAX];
+    __shared__ MomC<R> mc[2][LB_QMAX];
+    stage_consts(p, pc, mc, threadIdx.y * LB_BX + threadIdx.x, LB_BX * LB_BY);
+    __syncthreads();
+    const int2 d = p.block_desc[blockIdx.x];
+    const bool narrow = d.y & 1;
+    const int t = threadIdx.y * LB_BX + threadIdx.x;
+    const int x0 = d.x * LB_TILE_X + (narrow ? 2 * (t & 63) : 4 * threadIdx.x);
+    const int j = (d.y >> 1) + (narrow ? t >> 6 : threadIdx.y);
+    if (j >= p.ny || x0 >= p.nx) return;
+    const uint8_t flags = p.tmap[(size_t)j * p.ntx + d.x];
+    if (flags & LB_TILE_IFACE) return;   /* mode A interface rows: set by iface_kernel */
+    const int s = flags & LB_TILE_HIGH;
+    const int q = p.set[s].q;
+    constexpr bool PF = step_prefetch<ST>();
+    if (narrow) {
+        if (q == 9) step_cells<ST, 9, PF, 2>(p, s, flags, x0, j, pc[s], mc[s]);
+        else if (q == 16) step_cells<ST, 16, PF, 2>(p, s, flags, x0, j, pc[s], mc[s]);
+        else step_cells<ST, 36, PF, 2>(p, s, flags, x0, j, pc[s], mc[s]);
+    } else {
+        if (q == 9) step_cells<ST, 9, PF, 4>(p, s, flags, x0, j, pc[s], mc[s]);
+        else if (q == 16) step_cells<ST, 16, PF, 4>(p, s, flags, x0, j, pc[s], mc[s]);
+        else step_cells<ST, 36, PF, 4>(p, s, flags, x0, j, pc[s], mc[s]);
+    }
+}
+
+template <int ST>
+void launch_step_desc_store(const StepParams<typename Store<ST>::R> &p, int n, void *stream)
+{
+    static_assert(LB_BX * LB_BY == 64 * 4, "a narrow block is 4 rows of 64 threads");
+    if (n < 1) return;
+    step_desc_kernel<ST><<<n, dim3(LB_BX, LB_BY), 0, static_cast<cudaStream_t>(stream)>>>(p);
 }
 
 template <int ST>

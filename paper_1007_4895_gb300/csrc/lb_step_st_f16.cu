@@ -4,6 +4,7 @@
 
 namespace lbk {
 template void launch_step_store<3>(const StepParams<typename Store<3>::R> &, void *);
+template void launch_step_desc_store<3>(const StepParams<typename Store<3>::R> &, int, void *);
 template void launch_step_split_store<3>(const StepParams<typename Store<3>::R> &, int, const int2 *, int, void *, void *);
 template int launch_batch_store<3>(const void *, const int *, int, int, int, int, unsigned int *, int, int, void *);
 template int batch_blocks_per_sm<3>(int);

@@ -4,6 +4,7 @@
 
 namespace lbk {
 template void launch_step_store<2>(const StepParams<typename Store<2>::R> &, void *);
+template void launch_step_desc_store<2>(const StepParams<typename Store<2>::R> &, int, void *);
 template void launch_step_split_store<2>(const StepParams<typename Store<2>::R> &, int, const int2 *, int, void *, void *);
 template int launch_batch_store<2>(const void *, const int *, int, int, int, int, unsigned int *, int, int, void *);
 template int batch_blocks_per_sm<2>(int);

@@ -4,6 +4,7 @@
 
 namespace lbk {
 template void launch_step_store<0>(const StepParams<typename Store<0>::R> &, void *);
+template void launch_step_desc_store<0>(const StepParams<typename Store<0>::R> &, int, void *);
 template void launch_step_split_store<0>(const StepParams<typename Store<0>::R> &, int, const int2 *, int, void *, void *);
 template int launch_batch_store<0>(const void *, const int *, int, int, int, int, unsigned int *, int, int, void *);
 template int batch_blocks_per_sm<0>(int);

@@ -243,6 +243,43 @@ __device__ __forceinline__ void st4<__nv_bfloat16>(__nv_bfloat16 *p, const __nv_
     *reinterpret_cast<uint2 *>(p) = q;
 }
 
+template <typename T>
+__device__ __forceinline__ void st2(T *p, const T v[2]);
+template <>
+__device__ __forceinline__ void st2<float>(float *p, const float v[2])
+{
+    *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+}
+template <>
+__device__ __forceinline__ void st2<double>(double *p, const double v[2])
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+}
+template <>
+__device__ __forceinline__ void st2<__half>(__half *p, const __half v[2])
+{
+    *reinterpret_cast<__half2 *>(p) = __halves2half2(v[0], v[1]);
+}
+template <>
+__device__ __forceinline__ void st2<__nv_bfloat16>(__nv_bfloat16 *p, const __nv_bfloat16 v[2])
+{
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __halves2bfloat162(v[0], v[1]);
+}
+
+/* N = 2 or 4 consecutive elements (alignment as ld2 / ld4) */
+template <int N, typename T>
+__device__ __forceinline__ void ldn(const T *p, T v[N])
+{
+    if constexpr (N == 4) ld4(p, v);
+    else ld2(p, v);
+}
+template <int N, typename T>
+__device__ __forceinline__ void stn(T *p, const T v[N])
+{
+    if constexpr (N == 4) st4(p, v);
+    else st2(p, v);
+}
+
 /* minmod(a, b) = median(a, b, 0): the smaller-magnitude slope when both have one sign,
  * else 0 (the Sec. 3.1 limiter Psi(Theta) times the difference it multiplies). */
 __device__ __forceinline__ float minmod(float a, float b) { return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.0f)); }

@@ -132,7 +132,7 @@ def test_oscillating_wall_fp64():
     assert max(errs.values()) < F64_TOL, errs
 
 
-LAYOUTS = [0, 1, 2, 3, 4, 5]
+LAYOUTS = [0, 1, 2, 3, 4, 5, 6]
 
 
 @pytest.mark.parametrize("variant", LAYOUTS)
@@ -293,7 +293,7 @@ def test_long_channel_every_layout_matches_oracle(variant):
 
 
 @pytest.mark.parametrize("store", ["f64", "f32_dev", "bf16_dev", "bf16_dev_sr", "f16_dev_sr"])
-@pytest.mark.parametrize("variant", [2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [2, 3, 4, 5, 6])
 def test_register_block_layouts_equal_quad_layout(store, variant):
     """The split and streamed layouts do the quad layout's arithmetic in the same order,
     and draw the same random bits when rounding stochastically, so their populations
