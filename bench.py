@@ -195,31 +195,63 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def channel_lattices(lb, torch, store, variant=-1, rounding="nearest"):
+    """The channels of the workload, each on its own CUDA stream (independent problems,
+    as a user would run them: one channel's tail overlaps the next one's launch)."""
+    streams = [torch.cuda.Stream() for _ in workloads()]
+    lats = [lb.Lattice.from_workload(w, store=store, variant=variant, rounding=rounding, stream=s)
+            for w, s in zip(workloads(), streams)]
+    return lats, streams
+
+
+def timed_steps(torch, lats, streams, steps):
+    """CUDA events around `steps` steps of every channel: the start event on the current
+    stream is waited for by every channel stream, and the stop event follows all of
+    them. Returns milliseconds."""
+    main = torch.cuda.current_stream()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(main)
+    for s in streams:
+        s.wait_event(start)
+    for _ in range(steps):
+        for lat in lats:
+            lat.step(1)
+    for s in streams:
+        e = torch.cuda.Event()
+        e.record(s)
+        main.wait_event(e)
+    stop.record(main)
+    torch.cuda.synchronize()
+    return start.elapsed_time(stop)
+
+
+def launch_times(torch, lats, streams, reps):
+    """Per-launch durations of the step kernel, one launch at a time: events on the
+    launching stream, each launch ordered after the previous one's end event so that
+    nothing overlaps and no host gap falls inside a measurement."""
+    ev, prev = [], None
+    for _ in range(reps):
+        for i, (lat, s) in enumerate(zip(lats, streams)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if prev is not None:
+                s.wait_event(prev)
+            a.record(s)
+            lat.step(1)
+            b.record(s)
+            ev.append((i, a, b))
+            prev = b
+    torch.cuda.synchronize()
+    return [(i, a.elapsed_time(b)) for i, a, b in ev]
+
+
 def time_form(lb, torch, store, steps, warmup, variant=-1, with_kernel_times=True, rounding="nearest"):
-    lats = [lb.Lattice.from_workload(w, store=store, variant=variant, rounding=rounding) for w in workloads()]
+    lats, streams = channel_lattices(lb, torch, store, variant, rounding)
     for _ in range(warmup):
         for lat in lats:
             lat.step(1)
     torch.cuda.synchronize()
-    ev = []
-    start = torch.cuda.Event(enable_timing=True)
-    stop = torch.cuda.Event(enable_timing=True)
-    stride = max(1, steps // 200)
-    start.record()
-    for k in range(steps):
-        for i, lat in enumerate(lats):
-            if with_kernel_times and k % stride == 0:
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record()
-                lat.step(1)
-                b.record()
-                ev.append((i, a, b))
-            else:
-                lat.step(1)
-    stop.record()
-    torch.cuda.synchronize()
-    total_ms = start.elapsed_time(stop)
-    kern = [a.elapsed_time(b) for _, a, b in ev]
+    total_ms = timed_steps(torch, lats, streams, steps)
+    kern = [t for _, t in launch_times(torch, lats, streams, 20)] if with_kernel_times else []
     info = [lat.info() for lat in lats]
     eff = [lat.effective_map() for lat in lats]
     nbytes = [algorithmic_bytes(e, lat.sets, store) for e, lat in zip(eff, lats)]
@@ -251,23 +283,18 @@ def main():
         torch.cuda.synchronize()
 
     cells = sum(w.cells for w in workloads())
-    # main timed region: K steps of the three channels on this GPU
-    lats = [lb.Lattice.from_workload(w, store=args.store, variant=args.variant) for w in workloads()]
+    # main timed region: K steps of the three channels on this GPU, each channel on its
+    # own stream
+    lats, streams = channel_lattices(lb, torch, args.store, args.variant)
     for _ in range(args.warmup):
         for lat in lats:
             lat.step(1)
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    start.record()
-    for _ in range(args.steps):
-        for lat in lats:
-            lat.step(1)
-    stop.record()
+    ms = timed_steps(torch, lats, streams, args.steps)
     barrier()
     clk = clocks.stop()
-    ms = start.elapsed_time(stop)
     if dist is not None:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -277,19 +304,10 @@ def main():
     eff = [lat.effective_map() for lat in lats]
     nbytes = [algorithmic_bytes(e, lat.sets, args.store) for e, lat in zip(eff, lats)]
 
-    # per-launch durations of the step kernel, on its own stream (the lattices' stream)
-    kt = []
-    for _ in range(max(3, min(60, args.steps // 50))):
-        for i, lat in enumerate(lats):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            lat.step(1)
-            b.record()
-            kt.append((i, a, b))
-    torch.cuda.synchronize()
-    per = [a.elapsed_time(b) for _, a, b in kt]
-    avg_ms = statistics.mean(per)
-    avg_bytes = statistics.mean(nbytes[i] for i, _, _ in kt)
+    # per-launch durations of the step kernel, on the stream it is launched on
+    kt = launch_times(torch, lats, streams, max(3, min(60, args.steps // 50)))
+    avg_ms = statistics.mean(t for _, t in kt)
+    avg_bytes = statistics.mean(nbytes[i] for i, _ in kt)
     peak, peak_src = measured_peak_hbm()
     achieved = avg_bytes / (avg_ms / 1e3) / 1e9
     traffic = None
@@ -305,7 +323,7 @@ def main():
     # 3, equilibrium and force 8, four limited fluxes 28, update 6), peak = SMs x 128 FP32
     # lanes x the SM clock sampled during the timed region
     pops = [algorithmic_bytes(e, lat.sets, args.store) // (2 * STORE_BYTES[args.store]) for e, lat in zip(eff, lats)]
-    avg_pops = statistics.mean(pops[i] for i, _, _ in kt)
+    avg_pops = statistics.mean(pops[i] for i, _ in kt)
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
     alu_peak = nsm * 128 * sm_mhz * 1e6 / 1e9
@@ -316,7 +334,9 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "lbk::step kernel (one launch per channel per step)",
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, copy burst)",
-                "algorithmic_bytes_per_launch": avg_bytes, "launch_ms": avg_ms}
+                "algorithmic_bytes_per_launch": avg_bytes, "launch_ms": avg_ms,
+                "launches": "one at a time (isolated kernel durations)",
+                "whole_job_frac": sum(nbytes) * args.steps / (ms / 1e3) / 1e9 / peak}
 
     # end to end through the C ABI with host-resident state: per step, each channel's
     # state comes in from pinned host memory and its mass / residual goes back
@@ -331,6 +351,7 @@ def main():
         for lat, hbuf in zip(lats, host):
             lb.lb_state_load(lat.ctx, hbuf.data_ptr(), hbuf.numel())
             lat.step(1)
+        for lat in lats:
             lat.reductions()
     barrier()
     e2e_s = time.perf_counter() - t0
