@@ -208,9 +208,15 @@ int lb_get_populations(lb_ctx *ctx, int32_t set, double *dst);
  * (values at other nodes are ignored), then refreshes interface views. Synchronous. */
 int lb_set_populations(lb_ctx *ctx, int32_t set, const double *src);
 
-/* Raw state (both sets, current level, storage format) for checkpoints and
- * host-resident pipelines: lb_state_bytes gives the size; load / store copy it from /
- * to host memory on the context's stream (synchronous). */
+/* State of the current level for checkpoints and host-resident pipelines, in the
+ * storage format and compact: every node's populations in its own set only, tile row
+ * by tile row (the size follows from the map: sum over sets of Q_s x tile rows of s x
+ * 128 elements). Loading rebuilds what derives from it: ghost copies, mode-B shadow
+ * values, mode-A interface rows, pressure columns and carried moments, so a load
+ * followed by a step gives the same bits as the step that was never interrupted.
+ * lb_state_bytes gives the size; load / store copy from / to host memory through a
+ * device staging buffer of that size, on the context's stream (synchronous).
+ * LB_ERR_INVALID for a size that does not match. */
 int lb_state_bytes(lb_ctx *ctx, size_t *bytes);
 int lb_state_load(lb_ctx *ctx, const void *src, size_t bytes);
 int lb_state_store(lb_ctx *ctx, void *dst, size_t bytes);

@@ -103,6 +103,13 @@ struct lb_ctx {
     int *d_border = nullptr;
     size_t border_cap = 0;
     bool border_used = false;       /* false: the order is the raster order */
+    /* compact state (lb_state_*, lb_save / lb_load): one segment per tile row of a set */
+    std::vector<int4> seg_h;
+    int4 *d_seg = nullptr;
+    size_t seg_cap = 0;
+    int nseg[2] = {0, 0};
+    void *d_stage = nullptr;        /* device staging buffer of the compact state */
+    size_t stage_cap = 0;
     std::vector<int2> bdesc_h;      /* layout 6 block descriptors */
     int2 *d_bdesc = nullptr;
     size_t bdesc_cap = 0;
@@ -333,7 +340,9 @@ int finalize_level_t(lb_ctx *c, int level)
     if (c->opts.iface == LB_IFACE_HERMITE) lbk::launch_shadows<R>(c->store, p, st);
     lbk::launch_iface<R>(c->store, p, st);
     lbk::launch_pressure<R>(c->store, p, st);
-    lbk::launch_aux<R>(c->store, p, nullptr, 0, st);   /* carried moments of this level */
+    /* carried moments of this level: read only by layout 4 (and by the autotuner,
+     * which runs while no layout is chosen yet) */
+    if (c->variant < 0 || c->variant == 4) lbk::launch_aux<R>(c->store, p, nullptr, 0, st);
     return launch_check(c, "finalize");
 }
 
@@ -343,6 +352,45 @@ int finalize_level(lb_ctx *c, int level)
 }
 
 void *own(lb_ctx *c, size_t bytes);
+
+/* Compact state: every node's populations in its own set, one segment per tile row of
+ * a set (sets in order, rows and tiles ascending; mode-A interface rows are rebuilt, not
+ * stored). See pack_kernel for the byte layout. */
+void compact_segments(const lb_ctx *c, const std::vector<uint8_t> &tm, std::vector<int4> &seg, int nseg[2])
+{
+    seg.clear();
+    nseg[0] = nseg[1] = 0;
+    for (int s = 0; s < 2; ++s)
+        for (int j = 0; j < c->ny; ++j)
+            for (int tx = 0; tx < c->ntx; ++tx) {
+                const uint8_t f = tm[(size_t)j * c->ntx + tx];
+                if ((f & LB_TILE_IFACE) || (f & LB_TILE_HIGH) != s) continue;
+                seg.push_back(make_int4(tx, j, s, nseg[s]++));
+            }
+}
+
+size_t compact_bytes(const lb_ctx *c, const int nseg[2])
+{
+    return ((size_t)c->q[0] * nseg[0] + (size_t)c->q[1] * nseg[1]) * LB_TILE_X * c->esize;
+}
+
+/* the staging buffer of the compact state, grown as needed */
+int ensure_stage(lb_ctx *c, size_t bytes)
+{
+    if (bytes <= c->stage_cap) return LB_OK;
+    void *d = own(c, bytes);
+    if (!d) return fail(LB_ERR_NOMEM, "device allocation failed");
+    c->d_stage = d;
+    c->stage_cap = bytes;
+    return LB_OK;
+}
+
+template <typename R>
+void launch_pack_t(lb_ctx *c, int unpack)
+{
+    lbk::launch_pack<R>(c->store, make_params<R>(c, c->cur, c->cur, c->t), c->d_seg, c->nseg[0], c->nseg[1],
+                        std::max(c->q[0], c->q[1]), c->d_stage, unpack, c->stream);
+}
 
 /* Lists of the quads the plain kernels of the split step leave to the one-quad kernel:
  * every quad of a 4 x rb block that is not plain as a whole (plain_quad(), shared with
@@ -413,6 +461,19 @@ int build_edge_lists(lb_ctx *c)
         }
         if (int e = cuda_check(c, cudaMemcpyAsync(c->d_border, B.data(), B.size() * sizeof(int), cudaMemcpyHostToDevice,
                                                   c->stream), "block order upload"))
+            return e;
+    }
+    /* compact-state segments */
+    compact_segments(c, c->tmap, c->seg_h, c->nseg);
+    if (!c->seg_h.empty()) {
+        if (c->seg_h.size() > c->seg_cap) {
+            int4 *d = static_cast<int4 *>(own(c, c->seg_h.size() * sizeof(int4)));
+            if (!d) return fail(LB_ERR_NOMEM, "device allocation failed");
+            c->d_seg = d;
+            c->seg_cap = c->seg_h.size();
+        }
+        if (int e = cuda_check(c, cudaMemcpyAsync(c->d_seg, c->seg_h.data(), c->seg_h.size() * sizeof(int4),
+                                                  cudaMemcpyHostToDevice, c->stream), "segment list upload"))
             return e;
     }
     /* layout 6: a band of LB_STEP_BY rows holding a row of a set with 16 or more
@@ -1217,39 +1278,35 @@ int lb_set_populations(lb_ctx *c, int32_t set, const double *src)
 int lb_state_bytes(lb_ctx *c, size_t *bytes)
 {
     if (!c || !bytes) return fail(LB_ERR_INVALID, "null argument");
-    *bytes = c->set_bytes[0] + c->set_bytes[1];
+    *bytes = compact_bytes(c, c->nseg);
     return LB_OK;
 }
 
 int lb_state_load(lb_ctx *c, const void *src, size_t bytes)
 {
     if (int e = sticky(c)) return e;
-    if (!src || bytes != c->set_bytes[0] + c->set_bytes[1]) return fail(LB_ERR_INVALID, "state size mismatch");
-    const char *s = static_cast<const char *>(src);
-    if (int e = cuda_check(c, cudaMemcpyAsync(c->planes[c->cur][0], s, c->set_bytes[0], cudaMemcpyHostToDevice, c->stream),
-                           "state load"))
+    if (!src || bytes != compact_bytes(c, c->nseg)) return fail(LB_ERR_INVALID, "state size mismatch");
+    if (int e = ensure_stage(c, bytes)) return e;
+    if (int e = cuda_check(c, cudaMemcpyAsync(c->d_stage, src, bytes, cudaMemcpyHostToDevice, c->stream), "state load"))
         return e;
-    if (int e = cuda_check(c, cudaMemcpyAsync(c->planes[c->cur][1], s + c->set_bytes[0], c->set_bytes[1],
-                                              cudaMemcpyHostToDevice, c->stream), "state load"))
-        return e;
-    if (c->variant == 4) {   /* carried moments of the loaded level */
-        if (use_f64(c)) lbk::launch_aux<double>(c->store, make_params<double>(c, c->cur, c->cur, c->t), nullptr, 0, c->stream);
-        else lbk::launch_aux<float>(c->store, make_params<float>(c, c->cur, c->cur, c->t), nullptr, 0, c->stream);
-        if (int e = launch_check(c, "state load")) return e;
-    }
+    /* own-set populations with their ghost copies, then everything derived from them:
+     * shadows, interface rows, pressure columns, carried moments */
+    if (use_f64(c)) launch_pack_t<double>(c, 1);
+    else launch_pack_t<float>(c, 1);
+    if (int e = launch_check(c, "state load")) return e;
+    if (int e = finalize_level(c, c->cur)) return e;
     return cuda_check(c, cudaStreamSynchronize(c->stream), "state load sync");
 }
 
 int lb_state_store(lb_ctx *c, void *dst, size_t bytes)
 {
     if (int e = sticky(c)) return e;
-    if (!dst || bytes != c->set_bytes[0] + c->set_bytes[1]) return fail(LB_ERR_INVALID, "state size mismatch");
-    char *d = static_cast<char *>(dst);
-    if (int e = cuda_check(c, cudaMemcpyAsync(d, c->planes[c->cur][0], c->set_bytes[0], cudaMemcpyDeviceToHost, c->stream),
-                           "state store"))
-        return e;
-    if (int e = cuda_check(c, cudaMemcpyAsync(d + c->set_bytes[0], c->planes[c->cur][1], c->set_bytes[1],
-                                              cudaMemcpyDeviceToHost, c->stream), "state store"))
+    if (!dst || bytes != compact_bytes(c, c->nseg)) return fail(LB_ERR_INVALID, "state size mismatch");
+    if (int e = ensure_stage(c, bytes)) return e;
+    if (use_f64(c)) launch_pack_t<double>(c, 0);
+    else launch_pack_t<float>(c, 0);
+    if (int e = launch_check(c, "state store")) return e;
+    if (int e = cuda_check(c, cudaMemcpyAsync(dst, c->d_stage, bytes, cudaMemcpyDeviceToHost, c->stream), "state store"))
         return e;
     return cuda_check(c, cudaStreamSynchronize(c->stream), "state store sync");
 }
@@ -1266,13 +1323,13 @@ int lb_save(lb_ctx *c, const char *path)
 {
     if (int e = sticky(c)) return e;
     if (!path) return fail(LB_ERR_INVALID, "null path");
-    size_t bytes = c->set_bytes[0] + c->set_bytes[1];
+    size_t bytes = compact_bytes(c, c->nseg);
     std::vector<char> buf(bytes);
     if (int e = lb_state_store(c, buf.data(), bytes)) return e;
     lb_file_header hd;
     std::memset(&hd, 0, sizeof(hd));
     std::memcpy(hd.magic, "LBGBCKP", 8);
-    hd.version = 1;
+    hd.version = 2;   /* 2: compact state */
     hd.nx = c->nx; hd.ny = c->ny; hd.q0 = c->q[0]; hd.q1 = c->q[1]; hd.store = c->store; hd.iface = c->opts.iface;
     hd.step = c->step; hd.t = c->t; hd.dt = c->dt; hd.h = c->h; hd.rho0 = c->opts.rho0; hd.bytes = bytes;
     FILE *f = std::fopen(path, "wb");
@@ -1290,14 +1347,23 @@ int lb_load(lb_ctx *c, const char *path)
     FILE *f = std::fopen(path, "rb");
     if (!f) return fail(LB_ERR_INVALID, std::string("cannot open ") + path);
     lb_file_header hd;
-    size_t bytes = c->set_bytes[0] + c->set_bytes[1];
     std::vector<uint8_t> tm(c->tmap.size());
-    std::vector<char> buf(bytes);
     bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1;
-    ok = ok && std::memcmp(hd.magic, "LBGBCKP", 8) == 0 && hd.version == 1 && hd.nx == c->nx && hd.ny == c->ny &&
-         hd.q0 == c->q[0] && hd.q1 == c->q[1] && hd.store == c->store && hd.iface == c->opts.iface && hd.bytes == bytes &&
+    ok = ok && std::memcmp(hd.magic, "LBGBCKP", 8) == 0 && hd.version == 2 && hd.nx == c->nx && hd.ny == c->ny &&
+         hd.q0 == c->q[0] && hd.q1 == c->q[1] && hd.store == c->store && hd.iface == c->opts.iface &&
          hd.dt == c->dt && hd.h == c->h && hd.rho0 == c->opts.rho0;
-    ok = ok && std::fread(tm.data(), 1, tm.size(), f) == tm.size() && std::fread(buf.data(), 1, bytes, f) == bytes;
+    ok = ok && std::fread(tm.data(), 1, tm.size(), f) == tm.size();
+    /* the state's size follows from the stored map */
+    size_t bytes = 0;
+    if (ok) {
+        std::vector<int4> seg;
+        int nseg[2];
+        compact_segments(c, tm, seg, nseg);
+        bytes = compact_bytes(c, nseg);
+        ok = hd.bytes == bytes;
+    }
+    std::vector<char> buf(ok ? bytes : 0);
+    ok = ok && std::fread(buf.data(), 1, bytes, f) == bytes;
     std::fclose(f);
     if (!ok) return fail(LB_ERR_INVALID, "checkpoint does not match this lattice");
     c->tmap = tm;

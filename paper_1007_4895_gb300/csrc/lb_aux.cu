@@ -31,6 +31,44 @@ __global__ void init_kernel(const __grid_constant__ StepParams<typename Store<ST
         put1r(p, f + a * plane + (size_t)j * p.pitch, x, j, encode<ST>(deq(rd, r, c.cx[a] * u + c.cy[a] * v, usq), c.w[a], p.rho0));
 }
 
+/* Compact state: each node's populations in its own set and nothing else (shadows,
+ * ghosts, interface and pressure nodes and carried moments are rebuilt from them).
+ * seg[k] = (tile, row, set, index of the segment within its set): one tile row of a
+ * set, sets in order, rows and tiles ascending. Population a of segment k of set s
+ * sits at base_s + (a * nseg_s + k) * LB_TILE_X + column in the tile, with base_0 = 0,
+ * base_1 = q_0 nseg_0 LB_TILE_X; columns beyond nx hold zero. One block per
+ * (segment, population), one thread per column: both sides of every copy coalesce. */
+template <int ST>
+__global__ void pack_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p, const int4 *seg,
+                            int nseg0, int nseg1, typename Store<ST>::T *dst)
+{
+    using T = typename Store<ST>::T;
+    const int4 g = seg[blockIdx.x];
+    const int s = g.z, a = blockIdx.y;
+    if (a >= p.set[s].q) return;
+    const int x = g.x * LB_TILE_X + threadIdx.x;
+    const size_t base = s ? (size_t)p.set[0].q * nseg0 * LB_TILE_X : 0;
+    const size_t o = base + ((size_t)a * (s ? nseg1 : nseg0) + g.w) * LB_TILE_X + threadIdx.x;
+    const T *f = static_cast<const T *>(p.fin[s]) + a * p.plane + (size_t)g.y * p.pitch + LB_GHOST;
+    dst[o] = x < p.nx ? f[x] : T();
+}
+
+template <int ST>
+__global__ void unpack_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p, const int4 *seg,
+                              int nseg0, int nseg1, const typename Store<ST>::T *src)
+{
+    using T = typename Store<ST>::T;
+    const int4 g = seg[blockIdx.x];
+    const int s = g.z, a = blockIdx.y;
+    if (a >= p.set[s].q) return;
+    const int x = g.x * LB_TILE_X + threadIdx.x;
+    if (x >= p.nx) return;
+    const size_t base = s ? (size_t)p.set[0].q * nseg0 * LB_TILE_X : 0;
+    const size_t o = base + ((size_t)a * (s ? nseg1 : nseg0) + g.w) * LB_TILE_X + threadIdx.x;
+    T *f = static_cast<T *>(p.fout[s]) + a * p.plane + (size_t)g.y * p.pitch;
+    put1r(p, f, x, g.y, src[o]);
+}
+
 /* Canonical double [q][ny][nx] -> planes of set `set`, at nodes that use that set. */
 template <int ST>
 __global__ void set_pops_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p, int set,
@@ -310,6 +348,20 @@ void launch_init(int store, const StepParams<R> &p, const double *rho, const dou
 }
 
 template <typename R>
+void launch_pack(int store, const StepParams<R> &p, const int4 *seg, int nseg0, int nseg1, int qmax, void *dst,
+                 int unpack, void *stream)
+{
+    if (nseg0 + nseg1 < 1) return;
+    dim3 grid(nseg0 + nseg1, qmax);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) {
+        using T = typename Store<ST>::T;
+        if (unpack) unpack_kernel<ST><<<grid, LB_TILE_X, 0, st>>>(p, seg, nseg0, nseg1, static_cast<const T *>(dst));
+        else pack_kernel<ST><<<grid, LB_TILE_X, 0, st>>>(p, seg, nseg0, nseg1, static_cast<T *>(dst));
+    });
+}
+
+template <typename R>
 void launch_set_pops(int store, const StepParams<R> &p, int set, const double *src, void *stream)
 {
     dim3 grid((p.nx + 127) / 128, p.ny);
@@ -385,6 +437,8 @@ void launch_reduce(int store, const StepParams<R> &p, R *uprev, double *part, un
 
 template void launch_init<float>(int, const StepParams<float> &, const double *, const double *, const double *, void *);
 template void launch_init<double>(int, const StepParams<double> &, const double *, const double *, const double *, void *);
+template void launch_pack<float>(int, const StepParams<float> &, const int4 *, int, int, int, void *, int, void *);
+template void launch_pack<double>(int, const StepParams<double> &, const int4 *, int, int, int, void *, int, void *);
 template void launch_set_pops<float>(int, const StepParams<float> &, int, const double *, void *);
 template void launch_set_pops<double>(int, const StepParams<double> &, int, const double *, void *);
 template void launch_get_pops<float>(int, const StepParams<float> &, int, double *, void *);

@@ -154,6 +154,11 @@ void launch_init(int store, const StepParams<R> &p, const double *rho, const dou
                  void *stream);
 template <typename R>
 void launch_set_pops(int store, const StepParams<R> &p, int set, const double *src, void *stream);
+/* compact state (own-set populations only, segment list seg of nseg0 + nseg1 tile rows):
+ * pack p.fin into dst, or (unpack != 0) write dst into p.fout with ghost copies */
+template <typename R>
+void launch_pack(int store, const StepParams<R> &p, const int4 *seg, int nseg0, int nseg1, int qmax, void *dst,
+                 int unpack, void *stream);
 template <typename R>
 void launch_get_pops(int store, const StepParams<R> &p, int set, double *dst, void *stream);
 template <typename R>
