@@ -215,8 +215,12 @@ int lb_set_populations(lb_ctx *ctx, int32_t set, const double *src);
  * values, mode-A interface rows, pressure columns and carried moments, so a load
  * followed by a step gives the same bits as the step that was never interrupted.
  * lb_state_bytes gives the size; load / store copy from / to host memory through a
- * device staging buffer of that size, on the context's stream (synchronous).
- * LB_ERR_INVALID for a size that does not match. */
+ * device staging buffer of that size, on the context's stream. lb_state_store returns
+ * once dst holds the state. lb_state_load is asynchronous: it returns once the copy and
+ * the rebuild are queued, and src must stay valid and unchanged until the stream has
+ * passed them (lb_sync, or any later synchronous call on this context); from pinned
+ * memory the copy overlaps other streams' work. LB_ERR_INVALID for a size that does
+ * not match. */
 int lb_state_bytes(lb_ctx *ctx, size_t *bytes);
 int lb_state_load(lb_ctx *ctx, const void *src, size_t bytes);
 int lb_state_store(lb_ctx *ctx, void *dst, size_t bytes);

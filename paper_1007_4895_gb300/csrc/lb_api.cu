@@ -1294,8 +1294,7 @@ int lb_state_load(lb_ctx *c, const void *src, size_t bytes)
     if (use_f64(c)) launch_pack_t<double>(c, 1);
     else launch_pack_t<float>(c, 1);
     if (int e = launch_check(c, "state load")) return e;
-    if (int e = finalize_level(c, c->cur)) return e;
-    return cuda_check(c, cudaStreamSynchronize(c->stream), "state load sync");
+    return finalize_level(c, c->cur);   /* asynchronous: the caller keeps src until the stream passes */
 }
 
 int lb_state_store(lb_ctx *c, void *dst, size_t bytes)
@@ -1372,6 +1371,7 @@ int lb_load(lb_ctx *c, const char *path)
         if (c->tmap[(size_t)j * c->ntx] & LB_TILE_IFACE) c->iface_rows.push_back(j);
     if (int e = upload_tiles(c)) return e;
     if (int e = lb_state_load(c, buf.data(), bytes)) return e;
+    if (int e = cuda_check(c, cudaStreamSynchronize(c->stream), "load sync")) return e;   /* buf goes away */
     c->step = hd.step;
     c->t = hd.t;
     return LB_OK;
