@@ -36,37 +36,79 @@ __global__ void init_kernel(const __grid_constant__ StepParams<typename Store<ST
  * seg[k] = (tile, row, set, index of the segment within its set): one tile row of a
  * set, sets in order, rows and tiles ascending. Population a of segment k of set s
  * sits at base_s + (a * nseg_s + k) * LB_TILE_X + column in the tile, with base_0 = 0,
- * base_1 = q_0 nseg_0 LB_TILE_X; columns beyond nx hold zero. One block per
- * (segment, population), one thread per column: both sides of every copy coalesce. */
-template <int ST>
-__global__ void pack_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p, const int4 *seg,
-                            int nseg0, int nseg1, typename Store<ST>::T *dst)
+ * base_1 = q_0 nseg_0 LB_TILE_X; columns beyond nx hold zero.
+ * One warp per (set, population, segment) in the order of the compact buffer, four
+ * columns per lane: 16-byte vectors on both sides where the quad lies inside the
+ * lattice (and, unpacking, needs no ghost copy). Returns false for a warp past the end. */
+struct PackPos {
+    int s, a, tile, row;
+    size_t off;   /* element offset of this lane's four values in the compact buffer */
+};
+__device__ __forceinline__ bool pack_pos(const int4 *seg, int q0, int q1, int nseg0, int nseg1, PackPos &pp)
 {
-    using T = typename Store<ST>::T;
-    const int4 g = seg[blockIdx.x];
-    const int s = g.z, a = blockIdx.y;
-    if (a >= p.set[s].q) return;
-    const int x = g.x * LB_TILE_X + threadIdx.x;
-    const size_t base = s ? (size_t)p.set[0].q * nseg0 * LB_TILE_X : 0;
-    const size_t o = base + ((size_t)a * (s ? nseg1 : nseg0) + g.w) * LB_TILE_X + threadIdx.x;
-    const T *f = static_cast<const T *>(p.fin[s]) + a * p.plane + (size_t)g.y * p.pitch + LB_GHOST;
-    dst[o] = x < p.nx ? f[x] : T();
+    const size_t w = (size_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const size_t n0 = (size_t)q0 * nseg0;
+    size_t k;
+    if (w < n0) {
+        pp.s = 0;
+        pp.a = (int)(w / nseg0);
+        k = w % nseg0;
+    } else {
+        const size_t w1 = w - n0;
+        if (nseg1 == 0 || w1 >= (size_t)q1 * nseg1) return false;
+        pp.s = 1;
+        pp.a = (int)(w1 / nseg1);
+        k = nseg0 + w1 % nseg1;
+    }
+    const int4 g = seg[k];
+    pp.tile = g.x;
+    pp.row = g.y;
+    pp.off = w * LB_TILE_X + 4 * (threadIdx.x & 31);
+    return true;
 }
 
 template <int ST>
-__global__ void unpack_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p, const int4 *seg,
-                              int nseg0, int nseg1, const typename Store<ST>::T *src)
+__global__ void __launch_bounds__(256) pack_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p,
+                                                   const int4 *seg, int nseg0, int nseg1, typename Store<ST>::T *dst)
 {
     using T = typename Store<ST>::T;
-    const int4 g = seg[blockIdx.x];
-    const int s = g.z, a = blockIdx.y;
-    if (a >= p.set[s].q) return;
-    const int x = g.x * LB_TILE_X + threadIdx.x;
+    PackPos pp;
+    if (!pack_pos(seg, p.set[0].q, p.set[1].q, nseg0, nseg1, pp)) return;
+    const int x = pp.tile * LB_TILE_X + 4 * (threadIdx.x & 31);
+    const T *f = static_cast<const T *>(p.fin[pp.s]) + pp.a * p.plane + (size_t)pp.row * p.pitch + LB_GHOST + x;
+    T v[4];
+    if (x + 3 < p.nx) {
+        ld4(f, v);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = x + k < p.nx ? f[k] : T();
+    }
+    st4(dst + pp.off, v);
+}
+
+template <int ST>
+__global__ void __launch_bounds__(256) unpack_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p,
+                                                     const int4 *seg, int nseg0, int nseg1,
+                                                     const typename Store<ST>::T *src)
+{
+    using T = typename Store<ST>::T;
+    PackPos pp;
+    if (!pack_pos(seg, p.set[0].q, p.set[1].q, nseg0, nseg1, pp)) return;
+    const int x = pp.tile * LB_TILE_X + 4 * (threadIdx.x & 31);
     if (x >= p.nx) return;
-    const size_t base = s ? (size_t)p.set[0].q * nseg0 * LB_TILE_X : 0;
-    const size_t o = base + ((size_t)a * (s ? nseg1 : nseg0) + g.w) * LB_TILE_X + threadIdx.x;
-    T *f = static_cast<T *>(p.fout[s]) + a * p.plane + (size_t)g.y * p.pitch;
-    put1r(p, f, x, g.y, src[o]);
+    T v[4];
+    ld4(src + pp.off, v);
+    T *row = static_cast<T *>(p.fout[pp.s]) + pp.a * p.plane + (size_t)pp.row * p.pitch;
+    int img[2];
+    const bool plain = x + 3 < p.nx && row_images(p, pp.row, img) == 0 &&
+                       !(p.periodic_x && (x < LB_GHOST || x + 3 >= p.nx - LB_GHOST));
+    if (plain) {
+        st4(row + LB_GHOST + x, v);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (x + k < p.nx) put1r(p, row, x + k, pp.row, v[k]);
+    }
 }
 
 /* Canonical double [q][ny][nx] -> planes of set `set`, at nodes that use that set. */
@@ -181,8 +223,12 @@ __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Ste
         if (q == 9) node_moments<ST, 9>(f, plane, mcs[s], p.rho0, rd, jx, jy);
         else if (q == 16) node_moments<ST, 16>(f, plane, mcs[s], p.rho0, rd, jx, jy);
         else node_moments<ST, 36>(f, plane, mcs[s], p.rho0, rd, jx, jy);
+        /* u as the step forms it (one reciprocal in the arithmetic type); FP64 only for
+         * the sums: the FP64 rate is a small fraction of the FP32 rate here */
+        const R rr = p.rho0 + rd, inv = R(1) / rr;
+        const R uxr = jx * inv, uyr = jy * inv;
         const double rho = double(p.rho0) + double(rd);
-        const double ux = double(jx) / rho, uy = double(jy) / rho;
+        const double ux = double(uxr), uy = double(uyr);
         if (!isfinite(rho) || !isfinite(ux) || !isfinite(uy)) {
             acc[3] += 1.0;
             continue;
@@ -191,8 +237,8 @@ __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Ste
         acc[0] += rho;
         acc[1] += (ux - px) * (ux - px) + (uy - py) * (uy - py);
         acc[2] += ux * ux + uy * uy;
-        uprev[2 * n] = R(ux);
-        uprev[2 * n + 1] = R(uy);
+        uprev[2 * n] = uxr;
+        uprev[2 * n + 1] = uyr;
     }
     for (int m = 0; m < 4; ++m)
         for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_down_sync(0xffffffffu, acc[m], o);
@@ -351,13 +397,15 @@ template <typename R>
 void launch_pack(int store, const StepParams<R> &p, const int4 *seg, int nseg0, int nseg1, int qmax, void *dst,
                  int unpack, void *stream)
 {
-    if (nseg0 + nseg1 < 1) return;
-    dim3 grid(nseg0 + nseg1, qmax);
+    (void)qmax;
+    const size_t warps = (size_t)p.set[0].q * nseg0 + (size_t)p.set[1].q * nseg1;
+    if (warps == 0) return;
+    const unsigned grid = (unsigned)((warps + 7) / 8);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) {
         using T = typename Store<ST>::T;
-        if (unpack) unpack_kernel<ST><<<grid, LB_TILE_X, 0, st>>>(p, seg, nseg0, nseg1, static_cast<const T *>(dst));
-        else pack_kernel<ST><<<grid, LB_TILE_X, 0, st>>>(p, seg, nseg0, nseg1, static_cast<T *>(dst));
+        if (unpack) unpack_kernel<ST><<<grid, 256, 0, st>>>(p, seg, nseg0, nseg1, static_cast<const T *>(dst));
+        else pack_kernel<ST><<<grid, 256, 0, st>>>(p, seg, nseg0, nseg1, static_cast<T *>(dst));
     });
 }
 
