@@ -150,6 +150,7 @@ typedef struct {
     void (*free)(void *ptr, void *user);
     void *alloc_user;
     int32_t rounding;   /* LB_ROUND_NEAREST (0) or LB_ROUND_STOCHASTIC (1), see below */
+    const double *rho0_col;   /* NULL, or host [nx]: per-column reference density, see below */
 } lb_opts;
 
 /* Rounding of the updated populations into FP16 / BF16 deviation storage (other
@@ -161,11 +162,21 @@ typedef struct {
  * by boundary rules are rounded to nearest. */
 enum { LB_ROUND_NEAREST = 0, LB_ROUND_STOCHASTIC = 1 };
 
+/* Per-column reference density (deviation formats F32_DEV / F16_DEV / BF16_DEV only,
+ * else LB_ERR_INVALID): column x stores f / w - rho0_col[x] instead of f / w - rho0, so a
+ * lattice whose density varies along x (a pressure-driven channel) keeps small stored
+ * magnitudes and loses less to 16-bit rounding. The arithmetic and its results in FP32
+ * are those of one reference density; only the rounding of the stored values changes.
+ * Values must be finite and positive; the array is copied at create. Layouts 0 and 5
+ * support it (a forced other layout falls back to 0); batched lattices do not. The
+ * compact state (lb_state_*, checkpoints) holds the shifted values, so it belongs to a
+ * lattice with the same reference densities. */
+
 typedef struct lb_ctx lb_ctx;
 
 /* Creates a lattice.
  *   region_map: host [ny][nx], 0 = low-order set sets[0], 1 = high-order set sets[1].
- *     The library quantises it to tiles of 32 columns x 1 row: a tile uses the
+ *     The library quantises it to tiles of 128 columns x 1 row: a tile uses the
  *     high-order set if any of its nodes asks for it (lb_effective_map returns the
  *     result). Mode LB_IFACE_PAPER needs every row to use one set across x.
  *   sets: {low, high} population counts, each 9, 16 or 36.

@@ -69,7 +69,8 @@ class lb_opts(ctypes.Structure):
                 ("gx", ctypes.c_double), ("gy", ctypes.c_double), ("reduce_every", ctypes.c_int32),
                 ("variant", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_user", ctypes.c_void_p), ("rounding", ctypes.c_int32)]
+                ("alloc_user", ctypes.c_void_p), ("rounding", ctypes.c_int32),
+                ("rho0_col", ctypes.POINTER(ctypes.c_double))]
 
 
 def _load():
@@ -357,7 +358,8 @@ class Lattice:
 
     def __init__(self, nx, ny, region_map, sets=(9, 36), kn_ref=0.1, rho_ref=1.0, tau_mode=0, walls=None,
                  store="f32", iface="hermite", rho0=1.0, gx=0.0, gy=0.0, cfl=0.5, dt=0.0, h=0.0,
-                 reduce_every=0, stream=None, torch_allocator=True, variant=-1, rounding="nearest"):
+                 reduce_every=0, stream=None, torch_allocator=True, variant=-1, rounding="nearest",
+                 rho0_col=None):
         self.nx, self.ny = int(nx), int(ny)
         self.sets = tuple(int(s) for s in sets)
         self.store = STORES[store] if isinstance(store, str) else int(store)
@@ -375,6 +377,9 @@ class Lattice:
         opts.variant = int(variant)
         opts.rounding = ROUNDING[rounding] if isinstance(rounding, str) else int(rounding)
         opts.stream = sp
+        if rho0_col is not None:   # per-column reference density (deviation formats)
+            self._rho0_col = np.ascontiguousarray(np.asarray(rho0_col, dtype=np.float64).reshape(self.nx))
+            opts.rho0_col = self._rho0_col.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         if torch_allocator:
             self._alloc = _TorchAllocator(stream)
             opts.alloc, opts.free = self._alloc.alloc, self._alloc.free

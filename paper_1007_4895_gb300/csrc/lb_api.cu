@@ -114,6 +114,7 @@ struct lb_ctx {
     int2 *d_bdesc = nullptr;
     size_t bdesc_cap = 0;
     bool bdesc_narrow = false;      /* some band runs two nodes per thread */
+    void *d_dcol = nullptr;         /* per-column reference density: delta per storage column (R) */
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     /* learned placement */
     lb_mlp *mlp = nullptr;
@@ -214,6 +215,7 @@ StepParams<R> make_params(const lb_ctx *c, int in, int out, double t_new)
     p.step_key = (uint32_t)(c->step + (in != out ? 1 : 0));
     p.block_order = nullptr;   /* layout 5 sets it */
     p.block_desc = nullptr;    /* layout 6 sets it */
+    p.dcol = static_cast<const R *>(c->d_dcol);
     p.aux_in = c->aux[in];
     p.aux_out = c->aux[out];
     p.rho0 = R(c->opts.rho0);
@@ -603,6 +605,7 @@ void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
 /* layouts this context can run */
 bool variant_available(const lb_ctx *c, int v)
 {
+    if (c->d_dcol && v != 0 && v != 5) return false;   /* per-column reference density: layouts 0, 5 */
     if (v == 1) return c->tma_ok;
     if (v == 2 || v == 3) return c->edge_stream != nullptr;
     if (v == 4) return c->tma_ok && c->opts.iface == LB_IFACE_HERMITE;
@@ -623,6 +626,7 @@ int autotune_t(lb_ctx *c)
 {
     uint64_t hsh = 1469598103934665603ull;
     for (uint8_t b : c->tmap) hsh = (hsh ^ b) * 1099511628211ull;
+    if (c->d_dcol) hsh = (hsh ^ 0x9e3779b97f4a7c15ull) * 1099511628211ull;   /* fewer layouts available */
     TuneKey key{c->store, c->nx, c->ny, c->q[0], c->q[1], c->opts.iface, hsh};
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
@@ -917,6 +921,13 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
     if (opts->rounding != LB_ROUND_NEAREST && opts->rounding != LB_ROUND_STOCHASTIC)
         return fail(LB_ERR_INVALID, "unknown rounding mode");
     if (!(opts->rho0 > 0.0)) return fail(LB_ERR_INVALID, "rho0 must be positive");
+    if (opts->rho0_col) {
+        if (opts->store != LB_STORE_F32_DEV && opts->store != LB_STORE_F16_DEV && opts->store != LB_STORE_BF16_DEV)
+            return fail(LB_ERR_INVALID, "a per-column reference density needs a deviation storage format");
+        for (int x = 0; x < grid->nx; ++x)
+            if (!(opts->rho0_col[x] > 0.0) || !std::isfinite(opts->rho0_col[x]))
+                return fail(LB_ERR_INVALID, "per-column reference densities must be finite and positive");
+    }
     for (int k = 0; k < 4; ++k)
         if (walls[k].kind < LB_WALL_PERIODIC || walls[k].kind > LB_WALL_PRESSURE)
             return fail(LB_ERR_INVALID, "unknown wall kind");
@@ -988,8 +999,26 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
     const size_t rsize = use_f64(c) ? 8 : 4;
     for (int lv = 0; lv < 2; ++lv) c->aux[lv] = own(c, 3 * (size_t)c->pitch * c->ny * rsize);
     c->d_squeue = static_cast<unsigned int *>(own(c, 256));
-    bool ok = c->d_tmap && c->d_part && c->d_out && c->d_counter && c->d_uprev && c->d_err && c->aux[0] && c->aux[1] &&
-              c->d_squeue;
+    bool col_ok = true;
+    if (opts->rho0_col) {
+        /* delta = rho0(x) - rho0 per storage column; a ghost column takes the delta of the
+         * column it copies (periodic image, or the boundary column of a pressure side);
+         * the padding beyond holds 0 */
+        std::vector<float> dc(c->pitch, 0.0f);
+        const bool px = walls[2].kind == LB_WALL_PERIODIC;
+        for (int col = 0; col < c->nx + 2 * LB_GHOST; ++col) {
+            int x = col - LB_GHOST;
+            if (x < 0) x = px ? x + c->nx : 0;
+            if (x >= c->nx) x = px ? x - c->nx : c->nx - 1;
+            dc[col] = (float)(opts->rho0_col[x] - opts->rho0);
+        }
+        c->d_dcol = own(c, dc.size() * sizeof(float));
+        col_ok = c->d_dcol && cudaMemcpy(c->d_dcol, dc.data(), dc.size() * sizeof(float), cudaMemcpyHostToDevice) ==
+                                  cudaSuccess;
+        c->opts.rho0_col = nullptr;   /* the caller's array is not kept */
+    }
+    bool ok = col_ok && c->d_tmap && c->d_part && c->d_out && c->d_counter && c->d_uprev && c->d_err && c->aux[0] &&
+              c->aux[1] && c->d_squeue;
     for (int lv = 0; lv < 2; ++lv)
         for (int s = 0; s < 2; ++s) ok = ok && c->planes[lv][s];
     if (!ok) {
@@ -1515,6 +1544,7 @@ int lb_batch_create(int32_t n, const lb_grid *grids, const uint8_t *const *maps,
         if (o.reduce_every != 0) return fail(LB_ERR_INVALID, "batched lattices take no in-step reductions");
         if (o.store != opts[0].store || o.rho0 != opts[0].rho0)
             return fail(LB_ERR_INVALID, "batched lattices share the storage format and rho0");
+        if (o.rho0_col) return fail(LB_ERR_INVALID, "batched lattices take one reference density");
         for (int k = 0; k < 4; ++k) {
             const lb_wall &wl = walls[4 * (size_t)i + k];
             if (wl.kind == LB_WALL_PRESSURE) return fail(LB_ERR_INVALID, "batched lattices have no pressure sides");

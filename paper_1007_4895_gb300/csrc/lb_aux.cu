@@ -28,7 +28,8 @@ __global__ void init_kernel(const __grid_constant__ StepParams<typename Store<ST
     const size_t plane = p.plane;
     T *f = static_cast<T *>(p.fout[s]);
     for (int a = 0; a < c.q; ++a)
-        put1r(p, f + a * plane + (size_t)j * p.pitch, x, j, encode<ST>(deq(rd, r, c.cx[a] * u + c.cy[a] * v, usq), c.w[a], p.rho0));
+        put1r(p, f + a * plane + (size_t)j * p.pitch, x, j,
+              enc_at<ST>(p, deq(rd, r, c.cx[a] * u + c.cy[a] * v, usq), c.w[a], x + LB_GHOST));
 }
 
 /* Compact state: each node's populations in its own set and nothing else (shadows,
@@ -127,7 +128,7 @@ __global__ void set_pops_kernel(const __grid_constant__ StepParams<typename Stor
     for (int a = 0; a < c.q; ++a) {
         const double fv = src[((size_t)a * p.ny + j) * p.nx + x];
         const R d = R(fv * double(c.winv[a]) - double(p.rho0));
-        put1r(p, f + a * plane + (size_t)j * p.pitch, x, j, encode<ST>(d, c.w[a], p.rho0));
+        put1r(p, f + a * plane + (size_t)j * p.pitch, x, j, enc_at<ST>(p, d, c.w[a], x + LB_GHOST));
     }
 }
 
@@ -143,7 +144,7 @@ __global__ void get_pops_kernel(const __grid_constant__ StepParams<typename Stor
     const size_t plane = p.plane;
     const T *f = static_cast<const T *>(p.fin[set]) + (size_t)j * p.pitch + x + LB_GHOST;
     for (int a = 0; a < c.q; ++a) {
-        const R d = decode<ST>(f[a * plane], c.winv[a], p.rho0);
+        const R d = dec_at<ST>(p, f[a * plane], c.winv[a], x + LB_GHOST);
         dst[((size_t)a * p.ny + j) * p.nx + x] = double(c.w[a]) * (double(p.rho0) + double(d));
     }
 }
@@ -168,7 +169,7 @@ __global__ void moments_kernel(const __grid_constant__ StepParams<typename Store
     R d[LB_QMAX];
     R rd = R(0), jx = R(0), jy = R(0);
     for (int a = 0; a < c.q; ++a) {
-        d[a] = decode<ST>(f[a * plane], c.winv[a], rho0);
+        d[a] = dec_at<ST>(p, f[a * plane], c.winv[a], x + LB_GHOST);
         rd = fma(c.w[a], d[a], rd);
         jx = fma(c.wcx[a], d[a], jx);
         jy = fma(c.wcy[a], d[a], jy);
@@ -220,9 +221,9 @@ __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Ste
         const T *f = static_cast<const T *>(p.fin[s]) + (size_t)j * p.pitch + x + LB_GHOST;
         R rd, jx, jy;
         const int q = p.set[s].q;
-        if (q == 9) node_moments<ST, 9>(f, plane, mcs[s], p.rho0, rd, jx, jy);
-        else if (q == 16) node_moments<ST, 16>(f, plane, mcs[s], p.rho0, rd, jx, jy);
-        else node_moments<ST, 36>(f, plane, mcs[s], p.rho0, rd, jx, jy);
+        if (q == 9) node_moments<ST, 9>(f, plane, mcs[s], p.rho0, rd, jx, jy, p.dcol, x + LB_GHOST);
+        else if (q == 16) node_moments<ST, 16>(f, plane, mcs[s], p.rho0, rd, jx, jy, p.dcol, x + LB_GHOST);
+        else node_moments<ST, 36>(f, plane, mcs[s], p.rho0, rd, jx, jy, p.dcol, x + LB_GHOST);
         /* u as the step forms it (one reciprocal in the arithmetic type); FP64 only for
          * the sums: the FP64 rate is a small fraction of the FP32 rate here */
         const R rr = p.rho0 + rd, inv = R(1) / rr;
@@ -343,7 +344,7 @@ __global__ void hermite_residual_kernel(const __grid_constant__ StepParams<typen
     const T *f = static_cast<const T *>(p.fin[s]) + (size_t)j * p.pitch + x + LB_GHOST;
     R d[LB_QMAX], h[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     for (int a = 0; a < c.q; ++a) {
-        d[a] = decode<ST>(f[a * p.plane], c.winv[a], p.rho0);
+        d[a] = dec_at<ST>(p, f[a * p.plane], c.winv[a], x + LB_GHOST);
         hermite_acc(c, a, d[a], h);
     }
     R num = R(0);

@@ -36,19 +36,43 @@ __device__ __forceinline__ void stage_consts(const StepParams<R> &p, PopC<R> (*p
     }
 }
 
+/* Stored value at storage column c <-> deviation d, through the lattice's per-column
+ * reference density when it has one (p.dcol), else as decode / encode. */
+template <int ST>
+__device__ __forceinline__ typename Store<ST>::R dec_at(const StepParams<typename Store<ST>::R> &p,
+                                                       typename Store<ST>::T v, typename Store<ST>::R winv, int c)
+{
+    if constexpr (Store<ST>::dev) {
+        if (p.dcol) return decode_col<ST>(v, winv, p.rho0, p.dcol[c]);
+    }
+    return decode<ST>(v, winv, p.rho0);
+}
+template <int ST>
+__device__ __forceinline__ typename Store<ST>::T enc_at(const StepParams<typename Store<ST>::R> &p,
+                                                       typename Store<ST>::R d, typename Store<ST>::R w, int c)
+{
+    if constexpr (Store<ST>::dev) {
+        if (p.dcol) return encode_col<ST>(d, w, p.rho0, p.dcol[c]);
+    }
+    return encode<ST>(d, w, p.rho0);
+}
+
 /* sum w d, sum w xi_x d, sum w xi_y d of one node's stored populations (f[a * plane])
- * in population order: the moment pass of the step kernels. */
+ * in population order: the moment pass of the step kernels. dcol (may be NULL): the
+ * per-column reference density, the node at storage column c. */
 template <int ST, int Q>
 __device__ __forceinline__ void node_moments(const typename Store<ST>::T *f, size_t plane,
                                              const MomC<typename Store<ST>::R> *mc, typename Store<ST>::R rho0,
                                              typename Store<ST>::R &rd, typename Store<ST>::R &jx,
-                                             typename Store<ST>::R &jy)
+                                             typename Store<ST>::R &jy, const typename Store<ST>::R *dcol = nullptr,
+                                             int c = 0)
 {
     using R = typename Store<ST>::R;
     rd = jx = jy = R(0);
+    const R delta = dcol ? dcol[c] : R(0);
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        const R d = decode<ST>(f[a * plane], mc[a].winv, rho0);
+        const R d = dcol ? decode_col<ST>(f[a * plane], mc[a].winv, rho0, delta) : decode<ST>(f[a * plane], mc[a].winv, rho0);
         rd = fma(mc[a].w, d, rd);
         jx = fma(mc[a].wcx, d, jx);
         jy = fma(mc[a].wcy, d, jy);

@@ -70,6 +70,10 @@ struct StepParams {
      * per thread (bands holding high-order rows), h = 0: LB_STEP_BY rows, one quad per
      * thread */
     const int2 *block_desc;
+    /* per-column reference density (deviation formats): delta = rho0(x) - rho0 per
+     * storage column [pitch] (ghost columns hold the delta of the column they copy);
+     * NULL: one reference density */
+    const R *dcol;
     int sr;                         /* stochastic rounding of the updated populations */
     uint32_t step_key;              /* the step being computed (random-bit key) */
     R rho0, dt;

@@ -44,7 +44,7 @@ __global__ void iface_kernel(const __grid_constant__ StepParams<typename Store<S
         const T *f = static_cast<const T *>(p.fout[s]) + (size_t)rows[s] * p.pitch + x + LB_GHOST;
         R r = R(0), mx = R(0), my = R(0);
         for (int a = 0; a < c.q; ++a) {
-            R d = decode<ST>(f[a * plane], c.winv[a], rho0);
+            R d = dec_at<ST>(p, f[a * plane], c.winv[a], x + LB_GHOST);
             r = fma(c.w[a], d, r);
             mx = fma(c.wcx[a], d, mx);
             my = fma(c.wcy[a], d, my);
@@ -64,11 +64,11 @@ __global__ void iface_kernel(const __grid_constant__ StepParams<typename Store<S
         const int beyond = rows[1 - s];
         const R rn = rho0 + rhod[s], usn = u[s][0] * u[s][0] + u[s][1] * u[s][1];
         for (int a = 0; a < c.q; ++a) {
-            const R dnb = decode<ST>(fn[a * plane], c.winv[a], rho0);
+            const R dnb = dec_at<ST>(p, fn[a * plane], c.winv[a], x + LB_GHOST);
             const R eI = c.cx[a] * uIx + c.cy[a] * uIy;
             const R en = c.cx[a] * u[s][0] + c.cy[a] * u[s][1];
             const R d = deq(rIdev, rI, eI, usI) + (dnb - deq(rhod[s], rn, en, usn));
-            const T e = encode<ST>(d, c.w[a], rho0);
+            const T e = enc_at<ST>(p, d, c.w[a], x + LB_GHOST);
             put1r(p, fo + a * plane + (size_t)I * p.pitch, x, I, e);
             put1r(p, fo + a * plane + (size_t)beyond * p.pitch, x, beyond, e);
         }
@@ -117,13 +117,13 @@ __global__ void pressure_kernel(const __grid_constant__ StepParams<typename Stor
     if (is_pressure_node(p, xb, j)) {
         R d0 = R(0), d1 = R(0), r = R(0), mx = R(0), my = R(0);
         if (h0) {
-            d0 = decode<ST>(f[a0 * plane + xi], c.winv[a0], rho0);
+            d0 = dec_at<ST>(p, f[a0 * plane + xi], c.winv[a0], xi + LB_GHOST);
             r = c.w[a0] * d0;
             mx = c.wcx[a0] * d0;
             my = c.wcy[a0] * d0;
         }
         if (h1) {
-            d1 = decode<ST>(f[a1 * plane + xi], c.winv[a1], rho0);
+            d1 = dec_at<ST>(p, f[a1 * plane + xi], c.winv[a1], xi + LB_GHOST);
             r = fma(c.w[a1], d1, r);
             mx = fma(c.wcx[a1], d1, mx);
             my = fma(c.wcy[a1], d1, my);
@@ -136,7 +136,7 @@ __global__ void pressure_kernel(const __grid_constant__ StepParams<typename Stor
         auto put = [&](int a, R d) {
             const R e = c.cx[a] * uxn + c.cy[a] * uyn;
             const R dv = deq(rb - rho0, rb, e, usn) + (d - deq(r, rn, e, usn));
-            const T v = encode<ST>(dv, c.w[a], rho0);
+            const T v = enc_at<ST>(p, dv, c.w[a], xb + LB_GHOST);
             f[a * plane + xb] = v;
             for (int t = 0; t < nimg; ++t) f[a * plane + (ptrdiff_t)img[t] * p.pitch + xb] = v;
         };
@@ -148,7 +148,7 @@ __global__ void pressure_kernel(const __grid_constant__ StepParams<typename Stor
         R sr = R(0), sx = R(0), sy = R(0);
         for (int a = 0; a < q; ++a) {
             const T e = __shfl_sync(0xffffffffu, a < 32 ? e0 : e1, a & 31);
-            const R d = decode<ST>(e, c.winv[a], rho0);
+            const R d = dec_at<ST>(p, e, c.winv[a], xb + LB_GHOST);
             sr = fma(c.w[a], d, sr);
             sx = fma(c.wcx[a], d, sx);
             sy = fma(c.wcy[a], d, sy);
@@ -166,7 +166,7 @@ __global__ void pressure_kernel(const __grid_constant__ StepParams<typename Stor
     auto ghost = [&](int a) {
         const T e = f[a * plane + xb];
         for (int g = 1; g <= LB_GHOST; ++g) f[a * plane + (side == 0 ? xb - g : xb + g)] = e;
-        hermite_acc(c, a, decode<ST>(e, c.winv[a], rho0), hc);
+        hermite_acc(c, a, dec_at<ST>(p, e, c.winv[a], xb + LB_GHOST), hc);
     };
     if (h0) ghost(a0);
     if (h1) ghost(a1);
@@ -176,7 +176,7 @@ __global__ void pressure_kernel(const __grid_constant__ StepParams<typename Stor
         const SetConst<R> &ct = p.set[1 - s];
         T *ft = static_cast<T *>(p.fout[1 - s]) + (size_t)j * p.pitch + LB_GHOST;
         for (int b = lane; b < ct.q; b += 32) {
-            const T e = encode<ST>(hermite_rebuild(ct, b, hc), ct.w[b], rho0);
+            const T e = enc_at<ST>(p, hermite_rebuild(ct, b, hc), ct.w[b], xb + LB_GHOST);
             for (int g = 0; g <= LB_GHOST; ++g) ft[b * plane + (side == 0 ? xb - g : xb + g)] = e;
             for (int t = 0; t < nimg; ++t) ft[b * plane + (ptrdiff_t)img[t] * p.pitch + xb] = e;
         }
@@ -203,10 +203,10 @@ __global__ void shadows_kernel(const __grid_constant__ StepParams<typename Store
     const size_t plane = p.plane;
     const T *f = static_cast<const T *>(p.fout[s]) + (size_t)j * p.pitch + x + LB_GHOST;
     R h[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-    for (int a = 0; a < c.q; ++a) hermite_acc(c, a, decode<ST>(f[a * plane], c.winv[a], p.rho0), h);
+    for (int a = 0; a < c.q; ++a) hermite_acc(c, a, dec_at<ST>(p, f[a * plane], c.winv[a], x + LB_GHOST), h);
     T *ft = static_cast<T *>(p.fout[1 - s]);
     for (int b = 0; b < ct.q; ++b)
-        put1r(p, ft + b * plane + (size_t)j * p.pitch, x, j, encode<ST>(hermite_rebuild(ct, b, h), ct.w[b], p.rho0));
+        put1r(p, ft + b * plane + (size_t)j * p.pitch, x, j, enc_at<ST>(p, hermite_rebuild(ct, b, h), ct.w[b], x + LB_GHOST));
 }
 
 /* ------------------------------------------------------ carried moments -- */
@@ -246,9 +246,9 @@ __global__ void __launch_bounds__(128) aux_kernel(const __grid_constant__ StepPa
         const T *f = static_cast<const T *>(p.fout[s]) + (size_t)j * p.pitch + xi + LB_GHOST;
         R rd, jx, jy;
         const int q = p.set[s].q;
-        if (q == 9) node_moments<ST, 9>(f, p.plane, mcs[s], p.rho0, rd, jx, jy);
-        else if (q == 16) node_moments<ST, 16>(f, p.plane, mcs[s], p.rho0, rd, jx, jy);
-        else node_moments<ST, 36>(f, p.plane, mcs[s], p.rho0, rd, jx, jy);
+        if (q == 9) node_moments<ST, 9>(f, p.plane, mcs[s], p.rho0, rd, jx, jy, p.dcol, xi + LB_GHOST);
+        else if (q == 16) node_moments<ST, 16>(f, p.plane, mcs[s], p.rho0, rd, jx, jy, p.dcol, xi + LB_GHOST);
+        else node_moments<ST, 36>(f, p.plane, mcs[s], p.rho0, rd, jx, jy, p.dcol, xi + LB_GHOST);
         const size_t m = (size_t)j * p.pitch + xi;
         aout[m] = rd;
         aout[ap + m] = jx;

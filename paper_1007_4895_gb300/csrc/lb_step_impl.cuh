@@ -96,7 +96,7 @@ struct QuadStencil {
 
 /* PF: load population a + 1 while population a is computed (one-deep software
  * pipeline), for kernels whose threads are few and latency-bound. */
-template <int ST, int Q, bool PF = false, int NQ = 4>
+template <int ST, int Q, bool PF = false, int NQ = 4, bool COL = false>
 __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::R> &p, int s, uint8_t flags, int x0,
                                            int j, const PopC<typename Store<ST>::R> *pcs,
                                            const MomC<typename Store<ST>::R> *mcs)
@@ -113,6 +113,25 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
     const ptrdiff_t op1 = (ptrdiff_t)(row_at(p, j + 1) - j) * p.pitch;
     const ptrdiff_t op2 = (ptrdiff_t)(row_at(p, j + 2) - j) * p.pitch;
     const R rho0 = p.rho0;
+    /* COL: per-column reference density; dl[i] = delta at column x0 - 2 + i (node k at
+     * i = k + 2, its x neighbours l at 0, 1 and r at NQ + 2, NQ + 3) */
+    R dl[NQ + 4];
+    if constexpr (COL) {
+#pragma unroll
+        for (int i = 0; i < NQ + 4; ++i) dl[i] = p.dcol[x0 + LB_GHOST - 2 + i];
+    }
+    auto dec = [&](T raw, R winv, int i) -> R {
+        if constexpr (COL) return decode_col<ST>(raw, winv, rho0, dl[i]);
+        else return decode<ST>(raw, winv, rho0);
+    };
+    auto enc = [&](R d, R w, int i) -> T {
+        if constexpr (COL) return encode_col<ST>(d, w, rho0, dl[i]);
+        else return encode<ST>(d, w, rho0);
+    };
+    auto enc_sr = [&](R d, R w, int i, uint32_t bits) -> T {
+        if constexpr (COL) return encode_sr<ST>(d - dl[i], w, rho0, bits);
+        else return encode_sr<ST>(d, w, rho0, bits);
+    };
 
     /* 1. moments */
     R rhod[NQ], jx[NQ], jy[NQ];
@@ -125,7 +144,7 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
         const MomC<R> mc = mcs[a];
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
-            R d = decode<ST>(raw[k], mc.winv, rho0);
+            R d = dec(raw[k], mc.winv, k + 2);
             rhod[k] = fma(mc.w, d, rhod[k]);
             jx[k] = fma(mc.wcx, d, jx[k]);
             jy[k] = fma(mc.wcy, d, jy[k]);
@@ -167,8 +186,8 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
         T e[NQ];
 #pragma unroll
         for (int k = 0; k < NQ; ++k)
-            e[k] = (a >= 0 && p.sr) ? encode_sr<ST>(dn[k], w, rho0, sr_bits(x0 + k, j, p.nx, a, p.step_key))
-                                    : encode<ST>(dn[k], w, rho0);
+            e[k] = (a >= 0 && p.sr) ? enc_sr(dn[k], w, k + 2, sr_bits(x0 + k, j, p.nx, a, p.step_key))
+                                    : enc(dn[k], w, k + 2);
         for (int t = -1; t < nimg; ++t) {
             T *d = t < 0 ? dst : dst + (ptrdiff_t)img[t] * p.pitch;
             if (full && !near_x_edge) {
@@ -196,17 +215,17 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
             R v[NQ], l[2], r[2];
             ldn<NQ>(pa, raw);
     #pragma unroll
-            for (int k = 0; k < NQ; ++k) v[k] = decode<ST>(raw[k], winv, rho0);
+            for (int k = 0; k < NQ; ++k) v[k] = dec(raw[k], winv, k + 2);
             R Dx[NQ], Dy[NQ];
             const R crx = pc.crx, cry = pc.cry;
             if (crx != R(0)) {
                 T tl[2], tr[2];
                 ld2(pa - 2, tl);
                 ld2(pa + NQ, tr);
-                l[0] = decode<ST>(tl[0], winv, rho0);
-                l[1] = decode<ST>(tl[1], winv, rho0);
-                r[0] = decode<ST>(tr[0], winv, rho0);
-                r[1] = decode<ST>(tr[1], winv, rho0);
+                l[0] = dec(tl[0], winv, 0);
+                l[1] = dec(tl[1], winv, 1);
+                r[0] = dec(tr[0], winv, NQ + 2);
+                r[1] = dec(tr[1], winv, NQ + 3);
             }
             x_flux_diff<NQ>(crx, pc.kx, l, v, r, Dx);
             if (cry > R(0)) {
@@ -217,8 +236,8 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
                 const R kf = pc.ky;
     #pragma unroll
                 for (int k = 0; k < NQ; ++k) {
-                    R ym2 = decode<ST>(t2[k], winv, rho0), ym1 = decode<ST>(t1[k], winv, rho0);
-                    R yp1 = decode<ST>(tp[k], winv, rho0);
+                    R ym2 = dec(t2[k], winv, k + 2), ym1 = dec(t1[k], winv, k + 2);
+                    R yp1 = dec(tp[k], winv, k + 2);
                     R d0 = ym1 - ym2, d1 = v[k] - ym1, d2 = yp1 - v[k];
                     const R n1 = neg_part(d1);
                     Dy[k] = fma(kf, minmod_n(d1, d2, n1, neg_part(d2)) - minmod_n(d0, d1, neg_part(d0), n1), d1);
@@ -231,8 +250,8 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
                 const R kf = pc.ky;
     #pragma unroll
                 for (int k = 0; k < NQ; ++k) {
-                    R ym1 = decode<ST>(t1[k], winv, rho0), yp1 = decode<ST>(tp[k], winv, rho0);
-                    R yp2 = decode<ST>(t2[k], winv, rho0);
+                    R ym1 = dec(t1[k], winv, k + 2), yp1 = dec(tp[k], winv, k + 2);
+                    R yp2 = dec(t2[k], winv, k + 2);
                     R e0 = v[k] - ym1, e1 = yp1 - v[k], e2 = yp2 - yp1;
                     const R n1 = neg_part(e1);
                     Dy[k] = fma(-kf, minmod_n(e1, e2, n1, neg_part(e2)) - minmod_n(e0, e1, neg_part(e0), n1), e1);
@@ -299,22 +318,22 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
             const R winv = pc.winv;
             R v[NQ], l[2], r[2];
     #pragma unroll
-            for (int k = 0; k < NQ; ++k) v[k] = decode<ST>(cur.v[k], winv, rho0);
+            for (int k = 0; k < NQ; ++k) v[k] = dec(cur.v[k], winv, k + 2);
             R Dx[NQ], Dy[NQ];
             const R crx = pc.crx, cry = pc.cry;
             if (crx != R(0)) {
-                l[0] = decode<ST>(cur.l[0], winv, rho0);
-                l[1] = decode<ST>(cur.l[1], winv, rho0);
-                r[0] = decode<ST>(cur.r[0], winv, rho0);
-                r[1] = decode<ST>(cur.r[1], winv, rho0);
+                l[0] = dec(cur.l[0], winv, 0);
+                l[1] = dec(cur.l[1], winv, 1);
+                r[0] = dec(cur.r[0], winv, NQ + 2);
+                r[1] = dec(cur.r[1], winv, NQ + 3);
             }
             x_flux_diff<NQ>(crx, pc.kx, l, v, r, Dx);
             if (cry > R(0)) {
                 const R kf = pc.ky;
     #pragma unroll
                 for (int k = 0; k < NQ; ++k) {
-                    R ym2 = decode<ST>(cur.y0[k], winv, rho0), ym1 = decode<ST>(cur.y1[k], winv, rho0);
-                    R yp1 = decode<ST>(cur.y2[k], winv, rho0);
+                    R ym2 = dec(cur.y0[k], winv, k + 2), ym1 = dec(cur.y1[k], winv, k + 2);
+                    R yp1 = dec(cur.y2[k], winv, k + 2);
                     R d0 = ym1 - ym2, d1 = v[k] - ym1, d2 = yp1 - v[k];
                     const R n1 = neg_part(d1);
                     Dy[k] = fma(kf, minmod_n(d1, d2, n1, neg_part(d2)) - minmod_n(d0, d1, neg_part(d0), n1), d1);
@@ -323,8 +342,8 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
                 const R kf = pc.ky;
     #pragma unroll
                 for (int k = 0; k < NQ; ++k) {
-                    R ym1 = decode<ST>(cur.y0[k], winv, rho0), yp1 = decode<ST>(cur.y1[k], winv, rho0);
-                    R yp2 = decode<ST>(cur.y2[k], winv, rho0);
+                    R ym1 = dec(cur.y0[k], winv, k + 2), yp1 = dec(cur.y1[k], winv, k + 2);
+                    R yp2 = dec(cur.y2[k], winv, k + 2);
                     R e0 = v[k] - ym1, e1 = yp1 - v[k], e2 = yp2 - yp1;
                     const R n1 = neg_part(e1);
                     Dy[k] = fma(-kf, minmod_n(e1, e2, n1, neg_part(e2)) - minmod_n(e0, e1, neg_part(e0), n1), e1);
@@ -400,7 +419,7 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
             const T *pa = fout + a * plane + row0;
 #pragma unroll
             for (int k = 0; k < NQ; ++k)
-                if (valid[k]) hermite_acc(c, a, decode<ST>(pa[k], c.winv[a], rho0), h[k]);
+                if (valid[k]) hermite_acc(c, a, dec(pa[k], c.winv[a], k + 2), h[k]);
         }
         T *ftd = static_cast<T *>(p.fout[t]);
         const int qt = ct.q;
@@ -409,12 +428,14 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
             T *prow = ftd + b * plane + (size_t)j * p.pitch;
 #pragma unroll
             for (int k = 0; k < NQ; ++k)
-                if (valid[k]) put1r(p, prow, x0 + k, j, encode<ST>(hermite_rebuild(ct, b, h[k]), ct.w[b], rho0));
+                if (valid[k]) put1r(p, prow, x0 + k, j, enc(hermite_rebuild(ct, b, h[k]), ct.w[b], k + 2));
         }
     }
 }
 
-template <int ST>
+/* COL: the lattice has a per-column reference density (p.dcol); a separate kernel so
+ * that the common one keeps its register budget */
+template <int ST, bool COL = false>
 __global__ void __launch_bounds__(LB_BX *LB_BY, step_min_blocks<ST>()) step_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p)
 {
     using R = typename Store<ST>::R;
@@ -436,9 +457,9 @@ __global__ void __launch_bounds__(LB_BX *LB_BY, step_min_blocks<ST>()) step_kern
     const int s = flags & LB_TILE_HIGH;
     const int q = p.set[s].q;
     constexpr bool PF = step_prefetch<ST>();
-    if (q == 9) step_cells<ST, 9, PF>(p, s, flags, x0, j, pc[s], mc[s]);
-    else if (q == 16) step_cells<ST, 16, PF>(p, s, flags, x0, j, pc[s], mc[s]);
-    else step_cells<ST, 36, PF>(p, s, flags, x0, j, pc[s], mc[s]);
+    if (q == 9) step_cells<ST, 9, PF, 4, COL>(p, s, flags, x0, j, pc[s], mc[s]);
+    else if (q == 16) step_cells<ST, 16, PF, 4, COL>(p, s, flags, x0, j, pc[s], mc[s]);
+    else step_cells<ST, 36, PF, 4, COL>(p, s, flags, x0, j, pc[s], mc[s]);
 }
 
 
@@ -840,6 +861,12 @@ void launch_step_store(const StepParams<typename Store<ST>::R> &p, void *stream)
     dim3 block(LB_BX, LB_BY);
     dim3 grid((p.nx + 4 * LB_BX - 1) / (4 * LB_BX), (p.ny + LB_BY - 1) / LB_BY);
     if (p.block_order) grid = dim3(grid.x * grid.y, 1);
+    if constexpr (Store<ST>::dev) {
+        if (p.dcol) {
+            step_kernel<ST, true><<<grid, block, 0, static_cast<cudaStream_t>(stream)>>>(p);
+            return;
+        }
+    }
     step_kernel<ST><<<grid, block, 0, static_cast<cudaStream_t>(stream)>>>(p);
 }
 

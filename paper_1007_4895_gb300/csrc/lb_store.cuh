@@ -92,6 +92,25 @@ __device__ __forceinline__ typename Store<ST>::T encode(typename Store<ST>::R d,
     }
 }
 
+/* Per-column reference density (deviation formats only): the stored value is
+ * d - delta with delta = rho0(x) - rho0 of the node's column, so that a lattice whose
+ * density varies along x keeps small stored magnitudes. The arithmetic frame (d) is
+ * the same as without it. */
+template <int ST>
+__device__ __forceinline__ typename Store<ST>::R decode_col(typename Store<ST>::T v, typename Store<ST>::R winv,
+                                                           typename Store<ST>::R rho0, typename Store<ST>::R delta)
+{
+    if constexpr (Store<ST>::dev) return to_r(v) + delta;
+    else return decode<ST>(v, winv, rho0);
+}
+template <int ST>
+__device__ __forceinline__ typename Store<ST>::T encode_col(typename Store<ST>::R d, typename Store<ST>::R w,
+                                                           typename Store<ST>::R rho0, typename Store<ST>::R delta)
+{
+    if constexpr (Store<ST>::dev) return encode<ST>(d - delta, w, rho0);
+    else return encode<ST>(d, w, rho0);
+}
+
 /* ---- stochastic rounding of the 16-bit deviation formats ----
  * A per-step increment below half a unit in the last place of the stored deviation is
  * lost by round-to-nearest every step, and the state stagnates away from the solution.

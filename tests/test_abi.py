@@ -51,6 +51,9 @@ def _args(lb, nx=8, ny=8, **over):
     opts = lb.lb_opts()
     opts.store, opts.iface, opts.rho0 = over.get("store", 1), over.get("iface", 1), over.get("rho0", 1.0)
     opts.rounding = over.get("rounding", 0)
+    if "rho0_col" in over:
+        col = np.full(nx, 1.0) if over["rho0_col"] == "ones" else np.where(np.arange(nx) == 3, -1.0, 1.0)
+        opts.rho0_col = np.ascontiguousarray(col).ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     return grid, np.zeros((ny, nx), np.uint8), over.get("sets", (9, 36)), kn, walls, opts
 
 
@@ -58,6 +61,8 @@ def _args(lb, nx=8, ny=8, **over):
     dict(nx=2), dict(ny=3), dict(sets=(9, 25)), dict(store=9), dict(iface=5), dict(rho0=0.0), dict(kn=-1.0),
     dict(kn=1e-6),                                  # dt / tau > 1
     dict(rounding=2),                               # unknown rounding mode
+    dict(store=1, rho0_col="ones"),                 # per-column reference density: deviation formats only
+    dict(store=2, rho0_col="negative"),             # per-column reference densities must be positive
     dict(walls={0: None}),                          # bottom periodic, top diffuse (filled below)
 ])
 def test_invalid_arguments_are_rejected_on_the_host(lb, case):
@@ -103,7 +108,11 @@ def _batch_call(lb, n=2, **over):
         opts[i].store, opts[i].iface, opts[i].rho0 = 1, 1, 1.0
     for k, v in over.get("walls", {}).items():
         walls[4 + k] = v
+    keep = []
     for k, v in over.get("opts", {}).items():
+        if k == "rho0_col":
+            keep.append(np.ones(8))
+            v = keep[-1].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         setattr(opts[1], k, v)
     maps = [np.zeros((16, 8), np.uint8) for _ in range(n)]
     mp = (ctypes.c_void_p * n)(*[m.ctypes.data for m in maps])
@@ -117,6 +126,7 @@ def _batch_call(lb, n=2, **over):
     dict(opts={"reduce_every": 10}),                # no in-step reductions inside the batch
     dict(opts={"store": 2}),                        # one storage format for the batch
     dict(opts={"rho0": 2.0}),                       # one rest density for the batch
+    dict(opts={"rho0_col": "ones"}),                # one reference density per lattice
     dict(walls={1: "osc"}),                         # oscillating wall
     dict(walls={2: "pressure"}),                    # pressure side
 ])

@@ -203,6 +203,68 @@ def test_reduced_precision_channel(store):
         assert errs[k] < b, (k, errs)
 
 
+# Per-column reference density (lb_opts.rho0_col, the long channel's density estimate):
+# the stored deviation is f / w - rho0(x), so its magnitude, and the 16-bit rounding
+# error it carries, shrink where the density is far from one global rho0.
+def _col_pair(w, store, rho0_col, **kw):
+    import paper_1007_4895_gb300 as lb
+    a, o, eff = make_pair(w, store=store)
+    b = lb.Lattice.from_workload(w, store=store, rho0_col=rho0_col, **kw)
+    return a, b, o
+
+
+@pytest.mark.parametrize("store", ["f32_dev", "f16_dev", "bf16_dev"])
+@pytest.mark.parametrize("case", ["ragged", "pressure_channel"])
+def test_constant_per_column_reference_changes_nothing(store, case):
+    """rho0(x) = rho0 everywhere: every kernel that decodes or encodes goes through the
+    per-column path with a zero shift, and the populations and moments equal those of
+    the lattice without it."""
+    w = ragged_workload() if case == "ragged" else long_channel(nx=300, ny=37)
+    a, b, _ = _col_pair(w, store, np.full(w.nx, w.rho0))
+    a.step(40)
+    b.step(40)
+    own = a.effective_map()
+    for s in (0, 1):
+        pa, pb = a.populations(s), b.populations(s)
+        assert np.array_equal(pa[:, own == s], pb[:, own == s]), (store, case, s)
+    ma, mb = a.moments(), b.moments()
+    for k in ma:
+        assert np.array_equal(ma[k], mb[k]), (store, case, k)
+
+
+@pytest.mark.parametrize("store", ["f16_dev", "bf16_dev"])
+def test_per_column_reference_shrinks_16bit_error(store):
+    """Pressure channel with a 2:1 density drop, 16-bit storage with stochastic rounding
+    (with round-to-nearest the state also stagnates, which hides the noise). The
+    per-column reference rho0(x) = the density estimate takes the density offset out of
+    the stored deviation: against the FP64 oracle the density error falls well below
+    that of one rho0. The velocity part of the deviation, rho xi.u, is unchanged, so
+    the velocity error only has to be no worse."""
+    import paper_1007_4895_gb300 as lb
+    from lbinputs import long_channel_density
+    w = long_channel(nx=220, ny=40, steps=150)
+    _, b, o = _col_pair(w, store, long_channel_density(w.nx, 2.0, 1.0), rounding="stochastic")
+    a = lb.Lattice.from_workload(w, store=store, rounding="stochastic")
+    a.step(w.steps)
+    b.step(w.steps)
+    o.step(w.steps)
+    ref = o.moments()
+    ea, eb = field_errors(a.moments(), ref), field_errors(b.moments(), ref)
+    assert eb["rho"] < 0.6 * ea["rho"] and eb["u"] < ea["u"], (store, ea, eb)
+
+
+def test_per_column_reference_fp32_matches_oracle():
+    """FP32 deviations with rho0(x): the same FP32 accuracy as with one rho0."""
+    from lbinputs import long_channel_density
+    w = long_channel(nx=220, ny=40, steps=150)
+    a, b, o = _col_pair(w, "f32_dev", long_channel_density(w.nx, 2.0, 1.0))
+    b.step(w.steps)
+    o.step(w.steps)
+    e = field_errors(b.moments(), o.moments())
+    assert e["u"] < F32_VEL_TOL and e["rho"] < F32_VEL_TOL, e
+    assert b.info()["variant"] in (0, 5)
+
+
 # Stochastic rounding of the 16-bit stores (lb_opts.rounding): the expected stored value
 # equals the exact one, so increments below half an ulp are kept on average and the
 # stagnation bias above disappears; what remains is rounding noise of about one ulp of
