@@ -6,7 +6,8 @@ Python binding) never imports, links or runs anything here, and shares no code w
 
 The arithmetic lives in ``lb_oracle.c`` (plain loops, double precision, in the order the
 paper states the method); this module only compiles it with gcc and marshals arguments.
-``mlp.py`` holds the numpy FP64 oracle of the learned interface-placement network.
+``mlp.py`` holds the numpy FP64 oracle of the learned interface-placement network;
+``exact_stream.py`` the D2Q9 stream-and-collide reduction (Courant number one).
 """
 from __future__ import annotations
 
