@@ -151,7 +151,16 @@ typedef struct {
     void *alloc_user;
     int32_t rounding;   /* LB_ROUND_NEAREST (0) or LB_ROUND_STOCHASTIC (1), see below */
     const double *rho0_col;   /* NULL, or host [nx]: per-column reference density, see below */
+    int32_t scheme;     /* LB_SCHEME_TVD (0) or LB_SCHEME_STREAM (1), see below */
 } lb_opts;
+
+/* Update rule. LB_SCHEME_TVD: the Sec. 3.1 forward-Euler + TVD-minmod update, any sets,
+ * maps and walls. LB_SCHEME_STREAM: its D2Q9 reduction at Courant number one, where
+ * every population moves exactly one node per step and the update is the lattice BGK
+ * stream-and-collide (effective viscosity c_s^2 (tau - dt / 2)); needs sets[0] = 9, an
+ * all-zero region map, periodic walls on all four sides and dt = h / sqrt(3) (taken
+ * when grid.dt is 0; cfl is ignored), else LB_ERR_INVALID. */
+enum { LB_SCHEME_TVD = 0, LB_SCHEME_STREAM = 1 };
 
 /* Rounding of the updated populations into FP16 / BF16 deviation storage (other
  * formats ignore it). Nearest (ties to even) loses every per-step increment smaller

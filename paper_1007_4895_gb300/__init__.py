@@ -21,6 +21,8 @@ LIB_PATH = os.path.join(_HERE, "liblbgb.so")
 LB_OK, LB_ERR_INVALID, LB_ERR_NOMEM, LB_ERR_CUDA, LB_ERR_DIVERGED, LB_ERR_TIMEOUT = range(6)
 LB_ROUND_NEAREST, LB_ROUND_STOCHASTIC = 0, 1
 ROUNDING = {"nearest": LB_ROUND_NEAREST, "stochastic": LB_ROUND_STOCHASTIC}
+LB_SCHEME_TVD, LB_SCHEME_STREAM = 0, 1
+SCHEMES = {"tvd": LB_SCHEME_TVD, "stream": LB_SCHEME_STREAM}
 LB_STORE_F64, LB_STORE_F32, LB_STORE_F32_DEV, LB_STORE_F16_DEV, LB_STORE_BF16_DEV = range(5)
 LB_IFACE_PAPER, LB_IFACE_HERMITE = 0, 1
 LB_WALL_PERIODIC, LB_WALL_DIFFUSE, LB_WALL_PRESSURE = 0, 1, 2
@@ -70,7 +72,7 @@ class lb_opts(ctypes.Structure):
                 ("variant", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_user", ctypes.c_void_p), ("rounding", ctypes.c_int32),
-                ("rho0_col", ctypes.POINTER(ctypes.c_double))]
+                ("rho0_col", ctypes.POINTER(ctypes.c_double)), ("scheme", ctypes.c_int32)]
 
 
 def _load():
@@ -359,7 +361,7 @@ class Lattice:
     def __init__(self, nx, ny, region_map, sets=(9, 36), kn_ref=0.1, rho_ref=1.0, tau_mode=0, walls=None,
                  store="f32", iface="hermite", rho0=1.0, gx=0.0, gy=0.0, cfl=0.5, dt=0.0, h=0.0,
                  reduce_every=0, stream=None, torch_allocator=True, variant=-1, rounding="nearest",
-                 rho0_col=None):
+                 rho0_col=None, scheme="tvd"):
         self.nx, self.ny = int(nx), int(ny)
         self.sets = tuple(int(s) for s in sets)
         self.store = STORES[store] if isinstance(store, str) else int(store)
@@ -377,6 +379,7 @@ class Lattice:
         opts.variant = int(variant)
         opts.rounding = ROUNDING[rounding] if isinstance(rounding, str) else int(rounding)
         opts.stream = sp
+        opts.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         if rho0_col is not None:   # per-column reference density (deviation formats)
             self._rho0_col = np.ascontiguousarray(np.asarray(rho0_col, dtype=np.float64).reshape(self.nx))
             opts.rho0_col = self._rho0_col.ctypes.data_as(ctypes.POINTER(ctypes.c_double))

@@ -663,6 +663,7 @@ int autotune_t(lb_ctx *c)
 
 int choose_variant(lb_ctx *c)
 {
+    if (c->opts.scheme == LB_SCHEME_STREAM) return 0;   /* one kernel */
     if (c->opts.variant >= 0) return variant_available(c, c->opts.variant) ? c->opts.variant : 0;
     return use_f64(c) ? autotune_t<double>(c) : autotune_t<float>(c);
 }
@@ -746,9 +747,13 @@ int step_t(lb_ctx *c, int64_t n)
     for (int64_t k = 0; k < n; ++k) {
         const double t_new = c->t + c->dt;
         StepParams<R> p = make_params<R>(c, c->cur, c->cur ^ 1, t_new);
-        launch_variant<R>(c, c->variant, p);
-        lbk::launch_iface<R>(c->store, p, c->stream);
-        lbk::launch_pressure<R>(c->store, p, c->stream);
+        if (c->opts.scheme == LB_SCHEME_STREAM) {
+            lbk::launch_exact_stream<R>(c->store, p, c->stream);
+        } else {
+            launch_variant<R>(c, c->variant, p);
+            lbk::launch_iface<R>(c->store, p, c->stream);
+            lbk::launch_pressure<R>(c->store, p, c->stream);
+        }
         if (int e = launch_check(c, "step")) return e;
         c->cur ^= 1;
         c->t = t_new;
@@ -921,6 +926,15 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
     if (opts->rounding != LB_ROUND_NEAREST && opts->rounding != LB_ROUND_STOCHASTIC)
         return fail(LB_ERR_INVALID, "unknown rounding mode");
     if (!(opts->rho0 > 0.0)) return fail(LB_ERR_INVALID, "rho0 must be positive");
+    if (opts->scheme != LB_SCHEME_TVD && opts->scheme != LB_SCHEME_STREAM) return fail(LB_ERR_INVALID, "unknown scheme");
+    if (opts->scheme == LB_SCHEME_STREAM) {
+        if (sets[0] != 9) return fail(LB_ERR_INVALID, "the stream-and-collide scheme needs sets[0] = 9");
+        for (int k = 0; k < 4; ++k)
+            if (walls[k].kind != LB_WALL_PERIODIC)
+                return fail(LB_ERR_INVALID, "the stream-and-collide scheme needs periodic walls on every side");
+        for (size_t n = 0; n < (size_t)grid->nx * grid->ny; ++n)
+            if (region_map[n] != 0) return fail(LB_ERR_INVALID, "the stream-and-collide scheme takes one set (map all 0)");
+    }
     if (opts->rho0_col) {
         if (opts->store != LB_STORE_F32_DEV && opts->store != LB_STORE_F16_DEV && opts->store != LB_STORE_BF16_DEV)
             return fail(LB_ERR_INVALID, "a per-column reference density needs a deviation storage format");
@@ -953,6 +967,7 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
     c->store = opts->store;
     c->esize = elem_size(opts->store);
     c->stream = static_cast<cudaStream_t>(opts->stream);
+    const bool stream_scheme = opts->scheme == LB_SCHEME_STREAM;
     double xmax = 0.0;
     for (int s = 0; s < 2; ++s) {
         c->q[s] = sets[s];
@@ -960,10 +975,15 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
             delete c;
             return fail(LB_ERR_INVALID, "velocity sets must be 9, 16 or 36");
         }
+        if (stream_scheme && s == 1) continue;   /* one set in use */
         for (int a = 0; a < c->q[s]; ++a) xmax = std::fmax(xmax, std::fabs(c->cx[s][a]));
     }
     c->h = grid->h > 0.0 ? grid->h : (walls[0].kind == LB_WALL_PERIODIC ? 1.0 / grid->ny : 1.0 / (grid->ny - 1));
-    c->dt = grid->dt > 0.0 ? grid->dt : grid->cfl * c->h / xmax;
+    c->dt = grid->dt > 0.0 ? grid->dt : (stream_scheme ? c->h / xmax : grid->cfl * c->h / xmax);
+    if (stream_scheme && std::fabs(xmax * c->dt / c->h - 1.0) > 1e-12) {
+        delete c;
+        return fail(LB_ERR_INVALID, "the stream-and-collide scheme needs dt = h / sqrt(3)");
+    }
     if (!(c->dt > 0.0)) {
         delete c;
         return fail(LB_ERR_INVALID, "dt must be positive (cfl > 0 or dt > 0)");
@@ -1545,6 +1565,7 @@ int lb_batch_create(int32_t n, const lb_grid *grids, const uint8_t *const *maps,
         if (o.store != opts[0].store || o.rho0 != opts[0].rho0)
             return fail(LB_ERR_INVALID, "batched lattices share the storage format and rho0");
         if (o.rho0_col) return fail(LB_ERR_INVALID, "batched lattices take one reference density");
+        if (o.scheme != LB_SCHEME_TVD) return fail(LB_ERR_INVALID, "batched lattices use the TVD scheme");
         for (int k = 0; k < 4; ++k) {
             const lb_wall &wl = walls[4 * (size_t)i + k];
             if (wl.kind == LB_WALL_PRESSURE) return fail(LB_ERR_INVALID, "batched lattices have no pressure sides");

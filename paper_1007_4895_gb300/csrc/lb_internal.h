@@ -149,6 +149,9 @@ __host__ __device__ inline bool plain_quad(int x0, int j, uint8_t flags, int nx,
 }
 template <typename R>
 void launch_iface(int store, const StepParams<R> &p, void *stream);
+/* D2Q9 stream-and-collide step (Courant number one, periodic, one set) */
+template <typename R>
+void launch_exact_stream(int store, const StepParams<R> &p, void *stream);
 template <typename R>
 void launch_pressure(int store, const StepParams<R> &p, void *stream);
 template <typename R>

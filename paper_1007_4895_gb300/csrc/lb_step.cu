@@ -209,6 +209,56 @@ __global__ void shadows_kernel(const __grid_constant__ StepParams<typename Store
         put1r(p, ft + b * plane + (size_t)j * p.pitch, x, j, enc_at<ST>(p, hermite_rebuild(ct, b, h), ct.w[b], x + LB_GHOST));
 }
 
+/* ----------------------------------------------- D2Q9 stream and collide -- */
+
+/* The D2Q9 reduction of the Sec. 3.1 update at Courant number one (dt = h / sqrt(3),
+ * abscissae +-sqrt(3)): every population moves exactly one node along sign(xi) per step
+ * (stream), then relaxes towards Eq. (demoeq) with the Eq. (demoforce) force at the
+ * streamed state (collide). Periodic lattice of one set; one thread per node. The
+ * ghost rows and columns hold the periodic images, so the pull needs no index logic. */
+template <int ST>
+__global__ void __launch_bounds__(128) exact_stream_kernel(const __grid_constant__ StepParams<typename Store<ST>::R> p)
+{
+    using T = typename Store<ST>::T;
+    using R = typename Store<ST>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (x >= p.nx) return;
+    /* the population loops are unrolled, so the set's constants are read from the
+     * parameter block at fixed offsets; population a = 3 iy + ix over ascending
+     * abscissae moves by (ix - 1, iy - 1) */
+    const SetConst<R> &c = p.set[0];
+    const T *fin = static_cast<const T *>(p.fin[0]);
+    T *fout = static_cast<T *>(p.fout[0]);
+    const size_t plane = p.plane;
+    const R rho0 = p.rho0;
+    R d[9], rd = R(0), jx = R(0), jy = R(0);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const int sx = a % 3 - 1, sy = a / 3 - 1;
+        const int col = x - sx + LB_GHOST;
+        d[a] = dec_at<ST>(p, fin[a * plane + (ptrdiff_t)(j - sy) * p.pitch + col], c.winv[a], col);
+        rd = fma(c.w[a], d[a], rd);
+        jx = fma(c.wcx[a], d[a], jx);
+        jy = fma(c.wcy[a], d[a], jy);
+    }
+    const R rho = rho0 + rd, inv = R(1) / rho;
+    const R ux = jx * inv, uy = jy * inv;
+    const R usq = usq_of(ux, uy), om = p.dt / tau_of(p, rho), gu = xi_dot(p.gx, p.gy, ux, uy);
+    int img[2];
+    /* a node whose value has no ghost copy: stored once */
+    const bool plain = row_images(p, j, img) == 0 && x >= LB_GHOST && x < p.nx - LB_GHOST;
+    T *row = fout + (size_t)j * p.pitch;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const R eu = xi_dot(c.cx[a], c.cy[a], ux, uy);
+        R inc = om * (deq(rd, rho, eu, usq) - d[a]);
+        if (p.has_force) inc = force_inc(p.dt * rho, xi_dot(c.cx[a], c.cy[a], p.gx, p.gy), eu, gu, inc);
+        const T e = enc_at<ST>(p, d[a] + inc, c.w[a], x + LB_GHOST);
+        if (plain) row[a * plane + x + LB_GHOST] = e;
+        else put1r(p, row + a * plane, x, j, e);
+    }
+}
+
 /* ------------------------------------------------------ carried moments -- */
 
 /* Carried moments of the written level, sum w d, sum w xi_x d, sum w xi_y d per node
@@ -283,6 +333,14 @@ void launch_step(int store, const StepParams<R> &p, void *stream)
 }
 
 template <typename R>
+void launch_exact_stream(int store, const StepParams<R> &p, void *stream)
+{
+    dim3 grid((p.nx + 127) / 128, p.ny);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) exact_stream_kernel<ST><<<grid, 128, 0, st>>>(p));
+}
+
+template <typename R>
 void launch_step_desc(int store, const StepParams<R> &p, int n, void *stream)
 {
     LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) launch_step_desc_store<ST>(p, n, stream));
@@ -345,6 +403,8 @@ void launch_shadows(int store, const StepParams<R> &p, void *stream)
 
 template void launch_step<float>(int, const StepParams<float> &, void *);
 template void launch_step<double>(int, const StepParams<double> &, void *);
+template void launch_exact_stream<float>(int, const StepParams<float> &, void *);
+template void launch_exact_stream<double>(int, const StepParams<double> &, void *);
 template void launch_step_desc<float>(int, const StepParams<float> &, int, void *);
 template void launch_step_desc<double>(int, const StepParams<double> &, int, void *);
 template void launch_step_split<float>(int, const StepParams<float> &, int, const int2 *, int, void *, void *);

@@ -51,6 +51,7 @@ def _args(lb, nx=8, ny=8, **over):
     opts = lb.lb_opts()
     opts.store, opts.iface, opts.rho0 = over.get("store", 1), over.get("iface", 1), over.get("rho0", 1.0)
     opts.rounding = over.get("rounding", 0)
+    opts.scheme = over.get("scheme", 0)
     if "rho0_col" in over:
         col = np.full(nx, 1.0) if over["rho0_col"] == "ones" else np.where(np.arange(nx) == 3, -1.0, 1.0)
         opts.rho0_col = np.ascontiguousarray(col).ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -63,11 +64,16 @@ def _args(lb, nx=8, ny=8, **over):
     dict(rounding=2),                               # unknown rounding mode
     dict(store=1, rho0_col="ones"),                 # per-column reference density: deviation formats only
     dict(store=2, rho0_col="negative"),             # per-column reference densities must be positive
+    dict(scheme=2),                                 # unknown scheme
+    dict(scheme=1),                                 # stream-and-collide: walls must be periodic
+    dict(scheme=1, sets=(16, 36), walls="periodic"),    # stream-and-collide: D2Q9 only
     dict(walls={0: None}),                          # bottom periodic, top diffuse (filled below)
 ])
 def test_invalid_arguments_are_rejected_on_the_host(lb, case):
     over = dict(case)
-    if "walls" in over:
+    if over.get("walls") == "periodic":
+        over["walls"] = {0: lb.lb_wall(0, 0, 0, 1, 0), 1: lb.lb_wall(0, 0, 0, 1, 0)}
+    elif "walls" in over:
         over["walls"] = {0: lb.lb_wall(0, 0, 0, 1, 0)}
     nx, ny = over.pop("nx", 8), over.pop("ny", 8)
     args = _args(lb, nx, ny, **over)
