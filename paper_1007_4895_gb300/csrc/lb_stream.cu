@@ -296,7 +296,7 @@ __device__ __forceinline__ void stream_set(const Stream5Params<ST> &P, int s, in
                 }
                 if (wall_row[r]) {
                     const R xn = cya * (wall[r] == 0 ? R(1) : R(-1));
-                    if (xn > R(0)) continue;   /* gas-bound: written by the wall post-pass */
+                    if (xn > R(0)) continue;   /* gas-bound: set by the wall overwrite below */
                     if (xn < R(0)) {
 #pragma unroll
                         for (int k = 0; k < 4; ++k) LB5_EX(r, k, 0) = fma(-xn * pc.w, dn[k], LB5_EX(r, k, 0));

@@ -21,8 +21,9 @@ int launch_step3(int store, const StepParams<float> &p, const TmaMaps &maps, int
 int step3_rows();
 int step3_cols();
 int step3_planes();
-/* Streamed layout (4): TMA-fed single-pass kernel on carried moments (the boundary
- * post-passes follow it). FP32 / FP16 / BF16 storage. units: (tile, first row, rows,
+/* Streamed layout (4): TMA-fed single-pass kernel on carried moments, with the wall,
+ * ghost-row and mode-B work at the end of each unit (the pressure pass follows it).
+ * FP32 / FP16 / BF16 storage. units: (tile, first row, rows,
  * set) runs of one set, at most stream_rows() rows, most work first; queue: a device
  * counter (reset by the launch). 0 on launch, -1 if unavailable. */
 int launch_stream(int store, const StepParams<float> &p, const TmaMaps &maps, const int4 *units, int nunits,
