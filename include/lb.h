@@ -245,7 +245,10 @@ int lb_state_bytes(lb_ctx *ctx, size_t *bytes);
 int lb_state_load(lb_ctx *ctx, const void *src, size_t bytes);
 int lb_state_store(lb_ctx *ctx, void *dst, size_t bytes);
 
-/* Checkpoint file: header (grid, sets, storage, step, time) + raw state. */
+/* Checkpoint file: header (grid, sets, storage, step, time, a hash of the per-column
+ * reference densities) + the tile map + the compact state. lb_load returns
+ * LB_ERR_INVALID for a file of another lattice (grid, sets, storage, interface mode, dt,
+ * h, rho0 or reference densities differ). */
 int lb_save(lb_ctx *ctx, const char *path);
 int lb_load(lb_ctx *ctx, const char *path);
 

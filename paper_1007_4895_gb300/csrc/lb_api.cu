@@ -115,6 +115,7 @@ struct lb_ctx {
     size_t bdesc_cap = 0;
     bool bdesc_narrow = false;      /* some band runs two nodes per thread */
     void *d_dcol = nullptr;         /* per-column reference density: delta per storage column (R) */
+    uint32_t dcol_hash = 0;         /* FNV-1a of those deltas (0: one reference density) */
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     /* learned placement */
     lb_mlp *mlp = nullptr;
@@ -1032,6 +1033,13 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
             if (x >= c->nx) x = px ? x - c->nx : c->nx - 1;
             dc[col] = (float)(opts->rho0_col[x] - opts->rho0);
         }
+        uint32_t hsh = 2166136261u;
+        for (float v : dc) {
+            uint32_t b;
+            std::memcpy(&b, &v, 4);
+            for (int k = 0; k < 4; ++k) hsh = (hsh ^ ((b >> (8 * k)) & 0xffu)) * 16777619u;
+        }
+        c->dcol_hash = hsh ? hsh : 1u;
         c->d_dcol = own(c, dc.size() * sizeof(float));
         col_ok = c->d_dcol && cudaMemcpy(c->d_dcol, dc.data(), dc.size() * sizeof(float), cudaMemcpyHostToDevice) ==
                                   cudaSuccess;
@@ -1380,6 +1388,7 @@ int lb_save(lb_ctx *c, const char *path)
     hd.version = 2;   /* 2: compact state */
     hd.nx = c->nx; hd.ny = c->ny; hd.q0 = c->q[0]; hd.q1 = c->q[1]; hd.store = c->store; hd.iface = c->opts.iface;
     hd.step = c->step; hd.t = c->t; hd.dt = c->dt; hd.h = c->h; hd.rho0 = c->opts.rho0; hd.bytes = bytes;
+    hd.pad = (int32_t)c->dcol_hash;   /* the state's values are relative to these reference densities */
     FILE *f = std::fopen(path, "wb");
     if (!f) return fail(LB_ERR_INVALID, std::string("cannot open ") + path);
     bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 && std::fwrite(c->tmap.data(), 1, c->tmap.size(), f) == c->tmap.size() &&
@@ -1399,7 +1408,7 @@ int lb_load(lb_ctx *c, const char *path)
     bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1;
     ok = ok && std::memcmp(hd.magic, "LBGBCKP", 8) == 0 && hd.version == 2 && hd.nx == c->nx && hd.ny == c->ny &&
          hd.q0 == c->q[0] && hd.q1 == c->q[1] && hd.store == c->store && hd.iface == c->opts.iface &&
-         hd.dt == c->dt && hd.h == c->h && hd.rho0 == c->opts.rho0;
+         hd.dt == c->dt && hd.h == c->h && hd.rho0 == c->opts.rho0 && (uint32_t)hd.pad == c->dcol_hash;
     ok = ok && std::fread(tm.data(), 1, tm.size(), f) == tm.size();
     /* the state's size follows from the stored map */
     size_t bytes = 0;

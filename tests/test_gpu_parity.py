@@ -232,6 +232,30 @@ def test_constant_per_column_reference_changes_nothing(store, case):
         assert np.array_equal(ma[k], mb[k]), (store, case, k)
 
 
+def test_checkpoint_needs_the_same_reference_densities(tmp_path):
+    """A checkpoint holds values relative to the lattice's reference densities: it loads
+    into a lattice with the same rho0(x) (same bits after further steps) and is refused
+    by one with a single rho0."""
+    import paper_1007_4895_gb300 as lb
+    from lbinputs import long_channel_density
+    w = long_channel(nx=300, ny=37)
+    col = long_channel_density(w.nx, 2.0, 1.0)
+    a = lb.Lattice.from_workload(w, store="f16_dev", rho0_col=col)
+    a.step(11)
+    a.save(str(tmp_path / "ck.bin"))
+    a.step(7)
+    b = lb.Lattice.from_workload(w, store="f16_dev", rho0_col=col)
+    b.load(str(tmp_path / "ck.bin"))
+    b.step(7)
+    ma, mb = a.moments(), b.moments()
+    for k in ma:
+        assert np.array_equal(ma[k], mb[k]), k
+    c = lb.Lattice.from_workload(w, store="f16_dev")
+    with pytest.raises(lb.LBError) as e:
+        c.load(str(tmp_path / "ck.bin"))
+    assert e.value.code == lb.LB_ERR_INVALID
+
+
 @pytest.mark.parametrize("store", ["f16_dev", "bf16_dev"])
 def test_per_column_reference_shrinks_16bit_error(store):
     """Pressure channel with a 2:1 density drop, 16-bit storage with stochastic rounding
