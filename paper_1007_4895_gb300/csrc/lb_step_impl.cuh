@@ -180,6 +180,8 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
 
     int img[2];
     const int nimg = row_images(p, j, img);
+    /* a quad with no ghost copy (no image row, no ghost column, every node stored) */
+    const bool plain_store = nimg == 0 && full && !near_x_edge;
     /* a >= 0: an updated population (stochastically rounded when p.sr); a < 0: a value
      * set by the wall (rounded to nearest) */
     auto store_quad = [&](T *dst, const R dn[NQ], R w, int a) {
@@ -188,6 +190,10 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
         for (int k = 0; k < NQ; ++k)
             e[k] = (a >= 0 && p.sr) ? enc_sr(dn[k], w, k + 2, sr_bits(x0 + k, j, p.nx, a, p.step_key))
                                     : enc(dn[k], w, k + 2);
+        if (plain_store) {
+            stn<NQ>(dst, e);
+            return;
+        }
         for (int t = -1; t < nimg; ++t) {
             T *d = t < 0 ? dst : dst + (ptrdiff_t)img[t] * p.pitch;
             if (full && !near_x_edge) {
