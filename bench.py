@@ -159,6 +159,22 @@ def cpu_baseline(seconds=12.0):
             "sample": f"one 1024x512 channel (Kn 0.1) of the sweep, {n} steps, {dt:.1f} s, FP64, OpenMP"}
 
 
+def max_over_ranks(torch, dist, ms, device):
+    """The job's time: the slowest rank's (every rank gets it). Without a process group,
+    this rank's own."""
+    if dist is None:
+        return ms
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world, cells_per_rank, steps, ms):
+    """Whole-job throughput: every rank's cells (replicas of the same workload) over the
+    job's time."""
+    return world * cells_per_rank * steps / (ms / 1e3) / 1e6
+
+
 def run_reference(args, rank):
     """The oracle as the reference arm: each step advances a 64-column slab of each of
     the three channels (the flow is x-invariant, so a slab is the same problem)."""
@@ -295,11 +311,8 @@ def main():
     ms = timed_steps(torch, lats, streams, args.steps)
     barrier()
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * cells * args.steps / (ms / 1e3) / 1e6
+    ms = max_over_ranks(torch, dist, ms, "cuda")
+    value = job_mlups(world, cells, args.steps, ms)
     variants = [lat.info()["variant"] for lat in lats]
     eff = [lat.effective_map() for lat in lats]
     nbytes = [algorithmic_bytes(e, lat.sets, args.store) for e, lat in zip(eff, lats)]
