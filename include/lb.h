@@ -245,6 +245,13 @@ int lb_state_bytes(lb_ctx *ctx, size_t *bytes);
 int lb_state_load(lb_ctx *ctx, const void *src, size_t bytes);
 int lb_state_store(lb_ctx *ctx, void *dst, size_t bytes);
 
+/* Self-test of the bounded waits of the TMA-fed kernels: one thread waits on an
+ * mbarrier that nothing completes, gives up after `polls` polls (a poll takes tens of
+ * nanoseconds), records a code in a device word and returns; the host reads it back.
+ * *expired = 1 when the wait gave up as designed. Nothing faults or hangs: the kernel
+ * always returns. LB_ERR_CUDA if the launch or the copy failed. */
+int lb_selftest_bounded_wait(void *stream, uint32_t polls, int32_t *expired);
+
 /* Checkpoint file: header (grid, sets, storage, step, time, a hash of the per-column
  * reference densities) + the tile map + the compact state. lb_load returns
  * LB_ERR_INVALID for a file of another lattice (grid, sets, storage, interface mode, dt,

@@ -38,7 +38,8 @@ EXPORTS = ("lb_create", "lb_init_equilibrium", "lb_step", "lb_moments", "lb_redu
            "lb_reduce_fields_noalloc", "lb_features", "lb_hermite_residual", "lb_mlp_create", "lb_mlp_grad",
            "lb_mlp_adam_step", "lb_mlp_train", "lb_mlp_get_params", "lb_mlp_infer", "lb_mlp_destroy", "lb_set_mlp",
            "lb_learned_map_now", "lb_map_stats", "lb_batch_create", "lb_batch_step", "lb_batch_step_each",
-           "lb_batch_graph", "lb_batch_instance", "lb_batch_info", "lb_batch_sync", "lb_batch_destroy")
+           "lb_batch_graph", "lb_batch_instance", "lb_batch_info", "lb_batch_sync", "lb_batch_destroy",
+           "lb_selftest_bounded_wait")
 LB_NOALLOC_MAX_NODES = 524288
 
 
@@ -129,6 +130,7 @@ def _load():
     L.lb_batch_sync.argtypes = [P]
     L.lb_batch_destroy.argtypes = [P]
     L.lb_batch_destroy.restype = None
+    L.lb_selftest_bounded_wait.argtypes = [P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)]
     return L
 
 
@@ -207,6 +209,13 @@ def lb_state_bytes(ctx):
     n = ctypes.c_size_t()
     _check(_lib.lb_state_bytes(ctx, ctypes.byref(n)))
     return n.value
+
+
+def lb_selftest_bounded_wait(stream=None, polls=100000):
+    """True when a wait on a barrier that nothing completes gave up and reported it."""
+    out = ctypes.c_int32()
+    _check(_lib.lb_selftest_bounded_wait(ctypes.c_void_p(stream or 0), ctypes.c_uint32(polls), ctypes.byref(out)))
+    return bool(out.value)
 
 
 def lb_state_load(ctx, ptr, nbytes):

@@ -1435,6 +1435,31 @@ int lb_load(lb_ctx *c, const char *path)
     return LB_OK;
 }
 
+int lb_selftest_bounded_wait(void *stream, uint32_t polls, int32_t *expired)
+{
+    if (!expired) return fail(LB_ERR_INVALID, "null argument");
+    *expired = 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int *d = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LB_ERR_NOMEM, "device allocation failed");
+    }
+    const int code = 7;
+    int h = 0;
+    cudaError_t ce = cudaMemsetAsync(d, 0, sizeof(int), st);
+    if (ce == cudaSuccess && lbk::launch_wait_selftest(d, polls, code, st) != 0) ce = cudaErrorLaunchFailure;
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LB_ERR_CUDA, std::string("bounded-wait self-test: ") + cudaGetErrorString(ce));
+    }
+    *expired = h == code ? 1 : 0;
+    return LB_OK;
+}
+
 int lb_map_stats(lb_ctx *c, int64_t *updates, int64_t *fallbacks, double *high_fraction)
 {
     if (!c) return fail(LB_ERR_INVALID, "null context");

@@ -519,6 +519,23 @@ __global__ void __launch_bounds__(32 * (LB5_NC + 1), 1) stream_kernel(const __gr
 }
 
 
+/* Self-test of the bounded wait: one thread waits on an mbarrier that nothing
+ * completes, gives up after `polls` polls, records `code` in *err and returns. */
+__global__ void wait_selftest_kernel(int *err, uint32_t polls, int code)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_wait(&bar, 0, err, code, polls);
+}
+
+int launch_wait_selftest(int *err, uint32_t polls, int code, void *stream)
+{
+    wait_selftest_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(err, polls, code);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 template <int ST, bool FORCE>
 static int launch5(const StepParams<typename Store<ST>::R> &p, const TmaMaps &maps, const int4 *units, int nunits,
                    unsigned int *queue, int *err, void *stream)

@@ -46,10 +46,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0u;
 }
 
-/* bounded wait; on expiry sets *err (to `code`) and returns false */
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code)
+/* bounded wait (at most `limit` polls); on expiry sets *err (to `code`) and returns
+ * false */
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code,
+                                          uint32_t limit = LB_SPIN_LIMIT)
 {
-    for (uint32_t it = 0; it < LB_SPIN_LIMIT; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 1023u) == 1023u && *(volatile int *)err) return false;   /* another warp gave up */
     }

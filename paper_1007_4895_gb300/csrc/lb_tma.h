@@ -29,5 +29,7 @@ int step3_planes();
 int launch_stream(int store, const StepParams<float> &p, const TmaMaps &maps, const int4 *units, int nunits,
                   unsigned int *queue, int *err, void *stream);
 int stream_rows();   /* rows per work unit */
+/* bounded-wait self-test: err (device int) gets `code` once the wait gives up */
+int launch_wait_selftest(int *err, uint32_t polls, int code, void *stream);
 int stream_cols();   /* columns per plane tile: 128 + 2 x 4 ghost */
 }  // namespace lbk
