@@ -126,10 +126,13 @@ __device__ __forceinline__ R force_inc(R dt_rho, R gxi, R eu, R gu, R t)
     return fma(dt_rho, fma(gxi, eu, gxi) - gu, t);
 }
 
+/* tau of Eq. (KN): kn_ref rho_ref / rho (from inv = 1 / rho, already formed by every
+ * caller: a multiply instead of a second division), or the constant; minus dt / 2
+ * when tau_mode = 1 */
 template <typename R>
-__device__ __forceinline__ R tau_of(const StepParams<R> &p, R rho)
+__device__ __forceinline__ R tau_of(const StepParams<R> &p, R inv)
 {
-    R tau = p.tau_const ? p.kn_rho : p.kn_rho / rho;
+    const R tau = p.tau_const ? p.kn_rho : p.kn_rho * inv;
     return tau - p.tau_shift;
 }
 

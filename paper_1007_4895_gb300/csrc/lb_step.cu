@@ -243,9 +243,7 @@ __global__ void __launch_bounds__(128) exact_stream_kernel(const __grid_constant
     }
     const R rho = rho0 + rd, inv = R(1) / rho;
     const R ux = jx * inv, uy = jy * inv;
-    /* tau of Eq. (KN) from the reciprocal already formed (one division fewer) */
-    const R tau = (p.tau_const ? p.kn_rho : p.kn_rho * inv) - p.tau_shift;
-    const R usq = usq_of(ux, uy), om = p.dt / tau, gu = xi_dot(p.gx, p.gy, ux, uy);
+    const R usq = usq_of(ux, uy), om = p.dt / tau_of(p, inv), gu = xi_dot(p.gx, p.gy, ux, uy);
     int img[2];
     /* a node whose value has no ghost copy: stored once */
     const bool plain = row_images(p, j, img) == 0 && x >= LB_GHOST && x < p.nx - LB_GHOST;

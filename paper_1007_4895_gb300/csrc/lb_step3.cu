@@ -159,7 +159,7 @@ __device__ __forceinline__ void consume_set(const Tma3Params<ST> &P, int s, int 
         ux[m] *= inv;
         uy[m] *= inv;
         usq[m] = usq_of(ux[m], uy[m]);
-        om[m] = p.dt / tau_of(p, rho[m]);
+        om[m] = p.dt / tau_of(p, inv);
     }
 
     int wall = -1;

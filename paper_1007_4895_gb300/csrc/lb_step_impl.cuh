@@ -159,7 +159,7 @@ __device__ __forceinline__ void step_cells(const StepParams<typename Store<ST>::
         ux[k] = jx[k] * inv;
         uy[k] = jy[k] * inv;
         usq[k] = usq_of(ux[k], uy[k]);
-        om[k] = p.dt / tau_of(p, rho[k]);
+        om[k] = p.dt / tau_of(p, inv);
         gu[k] = xi_dot(p.gx, p.gy, ux[k], uy[k]);
     }
 
@@ -554,7 +554,7 @@ __device__ __forceinline__ void blk_cells(const StepParams<typename Store<ST>::R
             ux[r][k] *= inv;
             uy[r][k] *= inv;
             usq[r][k] = usq_of(ux[r][k], uy[r][k]);
-            om[r][k] = p.dt / tau_of(p, rho[r][k]);
+            om[r][k] = p.dt / tau_of(p, inv);
             if constexpr (FORCE) gu[r][k] = xi_dot(p.gx, p.gy, ux[r][k], uy[r][k]);
         }
 

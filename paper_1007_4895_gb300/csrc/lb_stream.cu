@@ -156,7 +156,7 @@ __device__ __forceinline__ void stream_set(const Stream5Params<ST> &P, int s, in
             ux[r][k] = jx[k] * inv;
             uy[r][k] = jy[k] * inv;
             usq[r][k] = usq_of(ux[r][k], uy[r][k]);
-            om[r][k] = p.dt / tau_of(p, rho[r][k]);
+            om[r][k] = p.dt / tau_of(p, inv);
             if constexpr (FORCE) gu[r][k] = xi_dot(p.gx, p.gy, ux[r][k], uy[r][k]);
         }
     }
