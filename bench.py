@@ -373,7 +373,7 @@ def main():
     barrier()
     e2e_s = time.perf_counter() - t0
     e2e = {"value": world * cells * e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
-           "h2d_bytes_per_step": int(sum(nbs)), "d2h_bytes_per_step": 4 * 8 * len(lats),
+           "h2d_bytes_per_step": int(sum(nbs)), "d2h_bytes_per_step": (4 * 8 + 4) * len(lats),
            "steps": e2e_steps}
     for lat in lats:
         lat.close()

@@ -1015,7 +1015,14 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
     for (int lv = 0; lv < 2; ++lv)
         for (int s = 0; s < 2; ++s) c->planes[lv][s] = own(c, c->set_bytes[s]);
     c->d_tmap = static_cast<uint8_t *>(own(c, c->tmap.size()));
-    c->red_blocks = lbk::reduce_blocks(c->nx, c->ny);
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            nsm = 0;
+        }
+        c->red_blocks = lbk::reduce_blocks(c->nx, c->ny, nsm);
+    }
     c->d_part = static_cast<double *>(own(c, sizeof(double) * 4 * c->red_blocks));
     c->d_out = static_cast<double *>(own(c, sizeof(double) * 4));
     c->d_counter = static_cast<unsigned int *>(own(c, 256));
@@ -1058,14 +1065,15 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
         delete c;
         return fail(LB_ERR_NOMEM, "device allocation failed");
     }
-    if (cudaMallocHost(reinterpret_cast<void **>(&c->h_out), 4 * sizeof(double)) != cudaSuccess ||
+    /* four doubles of results, then the device error word */
+    if (cudaMallocHost(reinterpret_cast<void **>(&c->h_out), 4 * sizeof(double) + 16) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->red_event, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         free_all(c);
         delete c;
         return fail(LB_ERR_CUDA, "pinned buffer / event creation failed");
     }
-    std::memset(c->h_out, 0, 4 * sizeof(double));
+    std::memset(c->h_out, 0, 4 * sizeof(double) + 16);
     /* second stream and fork / join events of the split step; without them that layout
      * is simply not offered */
     if (cudaStreamCreateWithFlags(&c->edge_stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1191,8 +1199,16 @@ int lb_reductions(lb_ctx *c, double out[4])
     if (int e = cuda_check(c, cudaMemcpyAsync(c->h_out, c->d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
                            "reduce copy"))
         return e;
+    /* the device error word comes back with the results: one wait for both */
+    int *h_err = reinterpret_cast<int *>(c->h_out + 4);
+    if (int e = cuda_check(c, cudaMemcpyAsync(h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                           "error word copy"))
+        return e;
     if (int e = cuda_check(c, cudaStreamSynchronize(c->stream), "reduce sync")) return e;
-    if (int e = check_device_error(c)) return fail(e, g_err);
+    if (*h_err != 0) {
+        c->status = LB_ERR_TIMEOUT;
+        return fail(c->status, "a bounded device wait ran out in the step kernel");
+    }
     c->red_pending = false;
     out[0] = c->h_out[0];
     out[1] = c->h_out[1];

@@ -467,11 +467,15 @@ template void launch_hermite_residual<float>(int, const StepParams<float> &, flo
 template void launch_hermite_residual<double>(int, const StepParams<double> &, float *, void *);
 
 /* One node per thread (at most 16384 blocks; larger lattices loop). */
-int reduce_blocks(int nx, int ny)
+int reduce_blocks(int nx, int ny, int nsm)
 {
+    /* four 256-thread blocks per SM: each thread sums several nodes before the FP64
+     * warp and block trees, whose cost per thread is fixed (the FP64 rate is a small
+     * fraction of the FP32 rate here) */
     long long n = (long long)nx * ny;
     long long b = (n + 255) / 256;
-    if (b > 16384) b = 16384;
+    const long long cap = nsm > 0 ? 4LL * nsm : 16384;
+    if (b > cap) b = cap;
     return (int)(b < 1 ? 1 : b);
 }
 

@@ -175,7 +175,7 @@ void launch_moments(int store, const StepParams<R> &p, uint32_t mask, void *dst,
 template <typename R>
 void launch_reduce(int store, const StepParams<R> &p, R *uprev, double *part, unsigned int *counter,
                    double *out, int nblocks, void *stream);
-int reduce_blocks(int nx, int ny);
+int reduce_blocks(int nx, int ny, int nsm);
 /* learned placement: features [8][ny][nx] from moment fields [9][ny][nx] (float) */
 template <typename R>
 void launch_features(const StepParams<R> &p, const float *moments, float *out, void *stream);
