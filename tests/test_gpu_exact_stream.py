@@ -31,23 +31,29 @@ def _start(nx, ny, seed=2):
     return rho, ux * np.ones((ny, nx)), uy * np.ones((ny, nx))
 
 
-def test_stream_scheme_fp64_populations_match_oracle():
-    nx, ny, steps = 200, 48, 120
+@pytest.mark.parametrize("nx,ny", [(200, 48), (203, 19), (37, 9), (1029, 6)])
+def test_stream_scheme_fp64_populations_match_oracle(nx, ny):
+    """Four nodes per thread with neighbours by warp shuffles: widths that end inside a
+    quad, inside a warp, and one warp past a block."""
+    steps = 120
+    kn = 0.02 * 48 / ny   # dt scales with 1 / ny: dt / tau about 0.6 at every size
     rho, ux, uy = _start(nx, ny)
-    lat = _box(nx, ny, "f64", kn_ref=0.02, rho_ref=1.0, gx=2e-3, gy=-1e-3, init=(rho, ux, uy))
+    lat = _box(nx, ny, "f64", kn_ref=kn, rho_ref=1.0, gx=2e-3, gy=-1e-3, init=(rho, ux, uy))
     assert np.isclose(lat.dt, lat.h / np.sqrt(3.0), rtol=1e-15)
     lat.step(steps)
-    f = es.run(es.equilibrium(rho, ux, uy), steps, dt=lat.dt, kn_ref=0.02, rho_ref=1.0, gx=2e-3, gy=-1e-3)
+    f = es.run(es.equilibrium(rho, ux, uy), steps, dt=lat.dt, kn_ref=kn, rho_ref=1.0, gx=2e-3, gy=-1e-3)
     got = lat.populations(0)
     assert np.max(np.abs(got - f)) / np.max(np.abs(f)) < 1e-12
 
 
-def test_stream_scheme_fp32_deviations_match_oracle():
-    nx, ny, steps = 200, 48, 120
+@pytest.mark.parametrize("nx,ny", [(200, 48), (203, 19)])
+def test_stream_scheme_fp32_deviations_match_oracle(nx, ny):
+    steps = 120
+    kn = 0.02 * 48 / ny
     rho, ux, uy = _start(nx, ny)
-    lat = _box(nx, ny, "f32_dev", kn_ref=0.02, rho_ref=1.0, gx=2e-3, init=(rho, ux, uy))
+    lat = _box(nx, ny, "f32_dev", kn_ref=kn, rho_ref=1.0, gx=2e-3, init=(rho, ux, uy))
     lat.step(steps)
-    f = es.run(es.equilibrium(rho, ux, uy), steps, dt=lat.dt, kn_ref=0.02, rho_ref=1.0, gx=2e-3)
+    f = es.run(es.equilibrium(rho, ux, uy), steps, dt=lat.dt, kn_ref=kn, rho_ref=1.0, gx=2e-3)
     r, u, v = es.moments(f)
     m = lat.moments()
     uref = np.max(np.hypot(u, v))
