@@ -97,6 +97,25 @@ def oscillatory_couette(nx=4, ny=64, rows=None, kn=0.1, u_wall_lat=0.05, stokes_
                "top": {"kind": "diffuse"}}, steps=steps)
 
 
+def kramers(ny=201, span=40.0, layer=10.0, u_lat=0.01, nx=4, sets=(9, 36), iface="hermite",
+            steps=2000) -> Workload:
+    """Kramers' problem (Sec. 3.3): a diffuse plate at rest at y = 0 and the shear imposed
+    by a diffuse plate moving at u_w at y = H, `span` mean free paths away (the paper's
+    200), far enough that the Knudsen layer of the resting plate does not reach it. The
+    high-order set covers y <= `layer` mean free paths (the paper's 10), the low-order
+    set the rest. The mean free path is lambda = tau = Kn (Eq. (KN) at rho = rho_ref) in
+    units of H, so Kn = 1 / span. Starts from the uniform shear u = u_w y / H."""
+    kn = 1.0 / span
+    rows = int(math.floor((ny - 1) * layer / span + 1e-9)) + 1
+    uw = lattice_speed(u_lat)
+    y = np.arange(ny) / (ny - 1)
+    ux = np.broadcast_to((uw * y)[:, None], (ny, nx)).copy()
+    return Workload(
+        name=f"kramers_{nx}x{ny}_span{span:g}", nx=nx, ny=ny, region_map=band_map(nx, ny, rows, 0),
+        sets=sets, kn_ref=kn, walls={"bottom": {"kind": "diffuse"}, "top": {"kind": "diffuse", "ux": uw}},
+        steps=steps, init=(np.ones((ny, nx)), ux, np.zeros((ny, nx))), iface=iface)
+
+
 def long_channel_density(nx: int, rho_in: float, rho_out: float) -> np.ndarray:
     """Isothermal lubrication estimate: rho^2 falls linearly from inlet to outlet."""
     x = np.arange(nx) / max(nx - 1, 1)

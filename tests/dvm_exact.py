@@ -69,3 +69,32 @@ def channel(n, tau, H=1.0, u_bottom=0.0, u_top=0.0, G=0.0):
         return out
 
     return u
+
+
+def half_space(n):
+    """Kramers' half-space problem (Sec. 3.3) for the linearised discrete-velocity model:
+    a diffuse plate at rest at y = 0 and a unit shear rate far from it. With lengths in
+    units of tau the solution is
+        g_j(y) = y + zeta - r_j + sum_m c_m exp(-lambda_m y) / (1 - lambda_m r_j),
+        u(y) = y + zeta + sum_m c_m exp(-lambda_m y),
+    the Chapman-Enskog bulk plus the decaying half-range modes; zeta (the slip
+    coefficient) and c_m follow from g_j(0) = 0 on every gas-bound abscissa r_j > 0
+    (as many equations as unknowns). Returns (zeta, lambdas, c, u) with u callable."""
+    r, w = rule(n)
+    lams = decay_rates(n)
+    pos = r[r > 1e-12]
+    A = np.zeros((len(pos), 1 + len(lams)))
+    A[:, 0] = 1.0
+    for m, l in enumerate(lams):
+        A[:, 1 + m] = 1.0 / (1.0 - l * pos)
+    sol = np.linalg.solve(A, pos)
+    zeta, c = float(sol[0]), sol[1:]
+
+    def u(y):
+        y = np.asarray(y, dtype=float)
+        out = y + zeta
+        for m, l in enumerate(lams):
+            out = out + c[m] * np.exp(-l * y)
+        return out
+
+    return zeta, np.array(lams), c, u
