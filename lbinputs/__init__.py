@@ -187,7 +187,7 @@ def placement_channel(kn: float, region_map=None, nx=8, ny=64, u_lat=0.05, cfl=0
     """Steady force-driven channel of the learned-placement study: periodic x, resting
     diffuse walls, the body force of a no-slip parabola with peak lattice speed u_lat,
     CFL 0.38 so that an all-high-order map is stable; region_map defaults to all
-    high-order (the judge)."""
+    high-order (the reference run)."""
     g = 8.0 * kn * lattice_speed(u_lat)
     w = poiseuille(nx=nx, ny=ny, rows=1, kn=kn, g_lat=g / (3.0 * (ny - 1)))
     w.region_map = np.ones((ny, nx), np.uint8) if region_map is None else np.asarray(region_map, np.uint8)

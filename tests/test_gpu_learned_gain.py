@@ -1,14 +1,14 @@
 """What the learned interface placement gains over the method without it.
 
 Steady force-driven channels (8 x 64, resting diffuse walls) across Knudsen numbers.
-The judge is the all-high-order (D2Q36) run; the method without the network is the
+The reference is the all-high-order (D2Q36) run; the method without the network is the
 fixed partition of the Sec. 3.4 tests (low-order set in the middle 70 %), i.e. 15 % of
 the rows next to each wall high-order.
-The network is trained on GPU with the library's kernels, on nodes of the judge runs
+The network is trained on GPU with the library's kernels, on nodes of the reference runs
 and of two fixed-map runs per Kn (features as those maps show them), labelled by the
-judge's beyond-second-order residual e3 = ||f - P2 f|| / rho > 3e-4 at that node. It
+reference run's beyond-second-order residual e3 = ||f - P2 f|| / rho > 3e-4 at that node. It
 then steers the map of runs that start from the fixed partition, including at Knudsen
-numbers it never saw. Velocity errors are e_u = max |u - u_judge| / max |u_judge|."""
+numbers it never saw. Velocity errors are e_u = max |u - u_ref| / max |u_ref|."""
 import numpy as np
 import pytest
 
@@ -60,10 +60,10 @@ def study():
     import paper_1007_4895_gb300 as lb
     from oracle import mlp as omlp
     allh = np.ones((NY, NX), np.uint8)
-    judge, X, E = {}, [], []
+    full, X, E = {}, [], []
     for kn in TRAIN_KN:
         lat, n = _run(kn, allh)
-        judge[kn] = (lat.moments(mask=0b111), n)
+        full[kn] = (lat.moments(mask=0b111), n)
         e3 = _residual(lat)
         X.append(_features(lat))
         E.append(e3)
@@ -83,12 +83,12 @@ def study():
     net.infer(xd, p)
     acc = float(((p.cpu().numpy() > 0.5) == (Y > 0.5)).mean())
     for kn in EVAL_KN:
-        if kn not in judge:
+        if kn not in full:
             lat, n = _run(kn, allh)
-            judge[kn] = (lat.moments(mask=0b111), n)
+            full[kn] = (lat.moments(mask=0b111), n)
     rows = []
     for kn in EVAL_KN:
-        ref, n = judge[kn]
+        ref, n = full[kn]
         fixed, _ = _run(kn, band_map(NX, NY, FIXED_ROWS), steps=n)
         learned, _ = _run(kn, band_map(NX, NY, FIXED_ROWS), steps=n, mlp=net)
         st = learned.map_stats()
