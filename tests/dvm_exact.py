@@ -30,10 +30,10 @@ def decay_rates(n):
     out = []
     for a, b in zip(edges[:-1], edges[1:]):
         xs = np.linspace(a * (1 + 1e-9), b * (1 - 1e-9), 100001)
-        v = np.array([f(x) for x in xs])
-        for k in range(len(xs) - 1):
-            if np.sign(v[k]) != np.sign(v[k + 1]) and abs(v[k]) < 1e6 and abs(v[k + 1]) < 1e6:
-                out.append(brentq(f, xs[k], xs[k + 1]))
+        v = np.sum(w[None, :] / (1.0 - xs[:, None] * r[None, :]), axis=1) - 1.0
+        # a sign change between finite samples (not across a pole)
+        ks = np.nonzero((np.sign(v[:-1]) != np.sign(v[1:])) & (np.abs(v[:-1]) < 1e6) & (np.abs(v[1:]) < 1e6))[0]
+        out.extend(brentq(f, xs[k], xs[k + 1]) for k in ks)
     return [x for x in out if x > 1e-6]
 
 
