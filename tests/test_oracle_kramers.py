@@ -1,12 +1,14 @@
 """The FP64 oracle on Kramers' problem (Sec. 3.3) against the exact steady solutions of
 the discrete-velocity model (``dvm_exact``): a plate at rest at y = 0, a plate moving at U
-20 mean free paths away, D2Q36 within 5 of the resting plate. The full-D2Q36 and
-full-D2Q9 lattices converge (first order in h: ghost = wall node) to their own two-plate
-solutions; the coupled one to the D2Q36 half-space layer joined to a D2Q9 plate, and in
-the Knudsen layer it follows the full-D2Q36 profile far closer than D2Q9 does."""
+20 mean free paths away, the high-order set (D2Q36, or D2Q16) within 5 of the resting
+plate. The full high-order and full-D2Q9 lattices converge (first order in h: ghost = wall node) to their own two-plate
+solutions; the coupled one to the high-order half-space layer joined to a D2Q9 plate, and
+in the Knudsen layer it follows the full high-order profile far closer than D2Q9 does."""
 import math
 
 import numpy as np
+
+import pytest
 
 import dvm_exact
 import oracle
@@ -16,48 +18,54 @@ SPAN, LAYER = 20.0, 5.0
 TAU = 1.0 / SPAN
 
 
-def _exact(model, U):
-    if model == "d2q36":
-        return dvm_exact.channel(6, TAU, u_bottom=0.0, u_top=U)
+N1D = {16: 4, 36: 6}
+
+
+def _exact(model, U, hi):
+    if model == "high":
+        return dvm_exact.channel(N1D[hi], TAU, u_bottom=0.0, u_top=U)
     if model == "d2q9":
         return dvm_exact.channel(3, TAU, u_bottom=0.0, u_top=U)
-    zeta, _, _, half = dvm_exact.half_space(6)
+    zeta, _, _, half = dvm_exact.half_space(N1D[hi])
     gamma = U / (1.0 + (zeta + math.sqrt(3.0)) * TAU)
     return lambda y: gamma * TAU * half(np.asarray(y) / TAU)
 
 
-def _steady(model, ny):
+def _steady(model, ny, hi):
     """14 time units from the predicted profile: 7 e-folds of the slowest diffusive mode
     (H^2 / (pi^2 nu), nu ~ tau = 0.05)."""
-    w = kramers(ny=ny, span=SPAN, layer=LAYER, u_lat=0.01)
+    w = kramers(ny=ny, span=SPAN, layer=LAYER, u_lat=0.01, sets=(9, hi))
     m = w.region_map.copy()
-    if model == "d2q36":
+    if model == "high":
         m[:] = 1
     elif model == "d2q9":
         m[:] = 0
     U = w.walls["top"]["ux"]
-    o = oracle.Oracle(w.nx, ny, m, n1d_lo=3, n1d_hi=6, kn_ref=w.kn_ref, rho_ref=w.rho_ref, walls=w.walls)
+    o = oracle.Oracle(w.nx, ny, m, n1d_lo=3, n1d_hi=N1D[hi], kn_ref=w.kn_ref, rho_ref=w.rho_ref, walls=w.walls)
     y = np.arange(ny) / (ny - 1)
-    o.init_equilibrium(1.0, np.broadcast_to(_exact(model, U)(y)[:, None], (ny, w.nx)), 0.0)
+    o.init_equilibrium(1.0, np.broadcast_to(_exact(model, U, hi)(y)[:, None], (ny, w.nx)), 0.0)
     o.step(int(round(14.0 / o.dt)))
     return y, o.moments()["ux"][:, 0], U
 
 
-def test_oracle_kramers_layer_against_exact_discrete_velocity_solutions():
+@pytest.mark.parametrize("hi", [36, 16])
+def test_oracle_kramers_layer_against_exact_discrete_velocity_solutions(hi):
+    """M-D2Q9-36 (the paper's pairing) and M-D2Q9-16."""
     ext = {}
-    for model in ("d2q36", "d2q9", "coupled"):
-        (yc, uc, U), (yf, uf, _) = _steady(model, 41), _steady(model, 81)
-        ex = _exact(model, U)
+    for model in ("high", "d2q9", "coupled"):
+        (yc, uc, U), (yf, uf, _) = _steady(model, 41, hi), _steady(model, 81, hi)
+        ex = _exact(model, U, hi)
         coarse = np.max(np.abs(uc - ex(yc))) / U
         fine = np.max(np.abs(uf - ex(yf))) / U
         ext[model] = 2.0 * uf[::2] - uc
         extrap = np.max(np.abs(ext[model] - ex(yc))) / U
-        # measured (relative to U): D2Q36 and coupled 1.0e-2 / 5.4e-3 / 1.3e-3, D2Q9
-        # 6.1e-3 / 3.2e-3 / 8.0e-4 (coarse / fine / extrapolated in h)
+        # measured (relative to U, coarse / fine / extrapolated in h): D2Q36 and M-D2Q9-36
+        # 1.0e-2 / 5.4e-3 / 1.3e-3, D2Q16 and M-D2Q9-16 9.1e-3 / 4.7e-3 / 1.1e-3, D2Q9
+        # 6.1e-3 / 3.2e-3 / 8.0e-4 (5.2e-3 / 2.7e-3 / 6.3e-4 at the D2Q16 time step)
         assert fine < 0.6 * coarse, (model, coarse, fine)
         assert extrap < 3e-3, (model, extrap)
     near = yc <= 3.0 * TAU
-    gap9 = np.max(np.abs(ext["d2q9"][near] - ext["d2q36"][near])) / U
-    gapc = np.max(np.abs(ext["coupled"][near] - ext["d2q36"][near])) / U
-    # measured: 3.1e-2 and 2.9e-3
+    gap9 = np.max(np.abs(ext["d2q9"][near] - ext["high"][near])) / U
+    gapc = np.max(np.abs(ext["coupled"][near] - ext["high"][near])) / U
+    # measured: 3.1e-2 and 2.9e-3 (D2Q36), 3.0e-2 and 3.1e-3 (D2Q16)
     assert gapc < 0.15 * gap9, (gapc, gap9)
