@@ -209,7 +209,11 @@ int lb_moments(lb_ctx *ctx, uint32_t mask, void *dst, int32_t dst_is_device, int
 /* Runs the reduction on the current level now and returns, synchronously,
  * out[0] = total mass sum rho (FP64), out[1] = residual ||u - u_prev|| / ||u|| against
  * the previous reduction (1 on the first call, which compares with u = 0),
- * out[2] = number of non-finite nodes, out[3] = step count. */
+ * out[2] = number of non-finite nodes, out[3] = step count. One wait on the context's
+ * stream brings back the results and the device error word together. Errors (sticky):
+ * LB_ERR_DIVERGED when a density or velocity is not finite, LB_ERR_TIMEOUT when a
+ * bounded device wait of an earlier step ran out, LB_ERR_CUDA when the launch or the
+ * copy failed. */
 int lb_reductions(lb_ctx *ctx, double out[4]);
 
 /* The tile-quantised map actually run, host [ny][nx] (0 / 1). */
