@@ -368,15 +368,19 @@ void lb_batch_destroy(lb_batch *b);
 
 /* Mass / residual reduction that allocates no device memory (the paper has no
  * counterpart: this is for callers that cannot allocate, e.g. code running under a
- * memory budget fixed by its host application, code whose allocator belongs to another
- * framework and cannot be reached from C, or code that must not allocate while it is
- * captured or replayed). It computes what lb_reductions computes, but on moment fields
+ * memory budget fixed by its host application, or code whose allocator belongs to
+ * another framework and cannot be reached from C). It computes what lb_reductions
+ * computes, but on moment fields
  * the caller owns (e.g. filled by lb_moments with dst_is_device = 1, dst_f64 = 1):
  *   rho, ux, uy: device double arrays of n nodes (1 <= n <= LB_NOALLOC_MAX_NODES);
  *   restart != 0: compare with u = 0 instead of the previous call's velocity;
  *   stream: cudaStream_t to run on (NULL = legacy default stream);
  *   out (host): [0] = sum rho (FP64), [1] = ||u - u_prev|| / ||u||, [2] = number of
- *     non-finite nodes, [3] = n. Synchronous.
+ *     non-finite nodes, [3] = n.
+ * Synchronous: it copies the result to the host and waits for the stream, so it must
+ * not be called while that stream is being captured into a CUDA graph. Every node's
+ * velocity is kept for the next call, a non-finite one included: after a call that
+ * found non-finite nodes, the next call's residual is non-finite unless restart != 0.
  * Returns LB_OK, LB_ERR_INVALID (null pointer, n out of range: nothing is launched),
  * LB_ERR_CUDA, or LB_ERR_DIVERGED (non-finite node; out is still filled); the message is
  * in lb_last_error().
@@ -384,7 +388,7 @@ void lb_batch_destroy(lb_batch *b);
  * (about 8.1 MB: per-block partial sums and the previous velocity of up to
  * LB_NOALLOC_MAX_NODES nodes), which every GPU that loads the library holds until the
  * process exits. The first call on a device looks up the array's device address on
- * that device; make that first call before any stream capture. All calls share the
+ * that device. All calls share the
  * array and it keeps the last call's velocity: calls that can overlap on the GPU (other
  * streams, other host threads) race with each other and must be serialised by the
  * caller. */

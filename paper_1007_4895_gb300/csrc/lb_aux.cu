@@ -232,12 +232,13 @@ __global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ Ste
         const double ux = double(uxr), uy = double(uyr);
         if (!isfinite(rho) || !isfinite(ux) || !isfinite(uy)) {
             acc[3] += 1.0;
-            continue;
+        } else {
+            const double px = double(uprev[2 * n]), py = double(uprev[2 * n + 1]);
+            acc[0] += rho;
+            acc[1] += (ux - px) * (ux - px) + (uy - py) * (uy - py);
+            acc[2] += ux * ux + uy * uy;
         }
-        const double px = double(uprev[2 * n]), py = double(uprev[2 * n + 1]);
-        acc[0] += rho;
-        acc[1] += (ux - px) * (ux - px) + (uy - py) * (uy - py);
-        acc[2] += ux * ux + uy * uy;
+        /* every node keeps this reduction's velocity, a non-finite one included */
         uprev[2 * n] = uxr;
         uprev[2 * n + 1] = uyr;
     }

@@ -3,9 +3,9 @@
  * memory.
  *
  * Some callers cannot call cudaMalloc or any allocating routine: code running inside a
- * memory budget fixed by its host application, code whose allocator is owned by another
- * framework and not reachable from C, or code that must not allocate while it is being
- * captured or replayed. For them lb_reduce_fields_noalloc does the work of the
+ * memory budget fixed by its host application, or code whose allocator is owned by
+ * another framework and not reachable from C. For them lb_reduce_fields_noalloc does
+ * the work of the
  * lb_reductions kernel on fields the caller already owns, and keeps everything else it
  * needs in one fixed scratch array that lives in this file:
  *   - per-block FP64 partial sums and the completion counter of the two-stage
@@ -15,6 +15,8 @@
  * it until the process exits. Host code never dereferences its name (on the host it is
  * only a stand-in); the device address is looked up once per device with
  * cudaGetSymbolAddress, with that device current, on the first call made on it.
+ * Every call is synchronous (it reads its result back to the host and waits for the
+ * stream), so it must not be called while its stream is being captured.
  */
 #include <cuda_runtime.h>
 
@@ -60,9 +62,11 @@ __global__ void noalloc_reduce_kernel(const double *rho, const double *ux, const
             acc[0] = r;
             acc[1] = (u - pu) * (u - pu) + (v - pv) * (v - pv);
             acc[2] = u * u + v * v;
-            scr->uprev[i][0] = u;
-            scr->uprev[i][1] = v;
         }
+        /* every node keeps this call's velocity, a non-finite one included, so that the
+         * next call never compares with a velocity older than the previous call */
+        scr->uprev[i][0] = u;
+        scr->uprev[i][1] = v;
     }
     for (int m = 0; m < 4; ++m)
         for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_down_sync(0xffffffffu, acc[m], o);
@@ -85,7 +89,7 @@ __global__ void noalloc_reduce_kernel(const double *rho, const double *ux, const
         __threadfence();
         double t[4] = {0.0, 0.0, 0.0, 0.0};
         for (unsigned b = 0; b < gridDim.x; ++b)
-            for (int m = 0; m < 4; ++m) t[m] += scr->part[b][m];
+            for (int m = 0; m < 4; ++m) t[m] += __ldcg(&scr->part[b][m]);   /* other blocks' partials, from L2 */
         scr->result[0] = t[0];
         scr->result[1] = t[2] > 0.0 ? sqrt(t[1] / t[2]) : 0.0;
         scr->result[2] = t[3];

@@ -1,8 +1,8 @@
 """lb_reduce_fields_noalloc: the mass / residual reduction for callers that cannot
-allocate device memory (a host application that fixes the memory budget, an allocator
-owned by another framework, code that must not allocate while it is captured or
-replayed). It keeps its partial sums and the previous velocity in a fixed array inside
-the library, so the caller passes only its input fields and a host output.
+allocate device memory (a host application that fixes the memory budget, or an
+allocator owned by another framework). It keeps its partial sums and the previous
+velocity in a fixed array inside the library, so the caller passes only its input
+fields and a host output.
 
 This file sorts last so that, in a run that stops at the first failure, every other
 test has already run."""
@@ -53,3 +53,32 @@ def test_matches_lb_reductions_on_two_calls_in_a_row():
     np.testing.assert_allclose(got2[0], ref2["mass"], rtol=tol)
     np.testing.assert_allclose(got2[1], ref2["residual"], rtol=tol)
     assert 0 < got2[1] < 1 and got2[2] == 0
+
+
+@pytest.mark.gpu
+def test_a_non_finite_node_is_reported_and_its_velocity_kept():
+    """A node that is non-finite on one call is counted and makes the call fail with
+    LB_ERR_DIVERGED; its velocity is still kept, so the next call (without restart)
+    compares with it and gives a non-finite residual; a restart clears that."""
+    import torch
+
+    import paper_1007_4895_gb300 as lb
+    n = 4096
+    g = torch.Generator(device="cpu").manual_seed(3)
+    rho = (1.0 + 0.01 * torch.rand(n, generator=g, dtype=torch.float64)).cuda()
+    ux = (0.01 * torch.rand(n, generator=g, dtype=torch.float64)).cuda()
+    uy = torch.zeros(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    args = (rho.data_ptr(), ux.data_ptr(), uy.data_ptr(), n)
+    ok = lb.lb_reduce_fields_noalloc(*args, restart=True, stream=stream)
+    assert ok[2] == 0
+    ux[17] = float("nan")
+    with pytest.raises(lb.LBError) as e:
+        lb.lb_reduce_fields_noalloc(*args, stream=stream)
+    assert e.value.code == lb.LB_ERR_DIVERGED
+    ux[17] = 0.005
+    again = lb.lb_reduce_fields_noalloc(*args, stream=stream)
+    assert again[2] == 0 and not np.isfinite(again[1])
+    fresh = lb.lb_reduce_fields_noalloc(*args, restart=True, stream=stream)
+    assert fresh[2] == 0 and np.isfinite(fresh[1])
+    np.testing.assert_allclose(fresh[0], rho.sum().item(), rtol=1e-12)
