@@ -115,6 +115,7 @@ struct lb_ctx {
     size_t bdesc_cap = 0;
     bool bdesc_narrow = false;      /* some band runs two nodes per thread */
     void *d_dcol = nullptr;         /* per-column reference density: delta per storage column (R) */
+    void *d_ctab = nullptr;         /* layouts 7 / 8: per-population constant tables */
     uint32_t dcol_hash = 0;         /* FNV-1a of those deltas (0: one reference density) */
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     /* learned placement */
@@ -217,6 +218,7 @@ StepParams<R> make_params(const lb_ctx *c, int in, int out, double t_new)
     p.block_order = nullptr;   /* layout 5 sets it */
     p.block_desc = nullptr;    /* layout 6 sets it */
     p.dcol = static_cast<const R *>(c->d_dcol);
+    p.ctab = c->d_ctab;
     p.aux_in = c->aux[in];
     p.aux_out = c->aux[out];
     p.rho0 = R(c->opts.rho0);
@@ -559,7 +561,8 @@ int upload_tiles(lb_ctx *c)
  * on 4 x 1 or 4 x 2 register blocks plus the one-quad kernel on the edge list
  * (lb_step_impl.cuh); 4: streamed (lb_stream.cu); 5: variant 0 with the blocks that
  * hold high-order rows launched first; 6: as 5, with two nodes per thread in the bands
- * that hold high-order rows. */
+ * that hold high-order rows; 7: layout 0's threads with paired FP32 arithmetic on the
+ * rows without boundary work (lb_pair.cuh); 8: 7 with the block order of 5. */
 template <typename R>
 void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
 {
@@ -588,6 +591,14 @@ void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
         }
         return;
     }
+    if constexpr (std::is_same<R, float>::value) {
+        if (variant == 7 || variant == 8) {
+            StepParams<R> q = p;
+            if (variant == 8 && c->border_used) q.block_order = c->d_border;
+            lbk::launch_pair(c->store, q, c->stream);
+            return;
+        }
+    }
     if (variant == 6 && c->bdesc_narrow) {
         StepParams<R> q = p;
         q.block_desc = c->d_bdesc;
@@ -606,7 +617,13 @@ void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
 /* layouts this context can run */
 bool variant_available(const lb_ctx *c, int v)
 {
-    if (c->d_dcol && v != 0 && v != 5) return false;   /* per-column reference density: layouts 0, 5 */
+    if (c->d_dcol && v != 0 && v != 5 && v != 7 && v != 8) return false;   /* per-column reference density */
+    if (v == 7 || v == 8) {
+        /* paired FP32 arithmetic: FP32 and 16-bit storage, 32-bit element offsets */
+        const size_t span = std::max(c->q[0], c->q[1]) * (size_t)(c->ny + 2 * LB_GHOST_ROWS) * c->pitch;
+        if (use_f64(c) || !c->d_ctab || span >= (1ull << 32)) return false;
+        return v == 7 || c->border_used;
+    }
     if (v == 1) return c->tma_ok;
     if (v == 2 || v == 3) return c->edge_stream != nullptr;
     if (v == 4) return c->tma_ok && c->opts.iface == LB_IFACE_HERMITE;
@@ -1098,6 +1115,11 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
         return fail(LB_ERR_CUDA, std::string("initial fill failed: ") + cudaGetErrorString(ce));
     }
     c->tma_ok = make_maps(c);
+    if (!use_f64(c)) {
+        /* constant tables of layouts 7 / 8 (without them those layouts are not offered) */
+        c->d_ctab = own(c, lbk::pair_table_bytes());
+        if (c->d_ctab) lbk::launch_pair_table(make_params<float>(c, 0, 1, 0.0), c->d_ctab, c->stream);
+    }
     *out = c;
     e = lb_init_equilibrium(c, nullptr, nullptr, nullptr);
     if (e) {

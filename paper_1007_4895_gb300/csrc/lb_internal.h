@@ -74,6 +74,9 @@ struct StepParams {
      * storage column [pitch] (ghost columns hold the delta of the column they copy);
      * NULL: one reference density */
     const R *dcol;
+    /* layouts 7 / 8: the per-population constant tables in device memory, built once per
+     * lattice by launch_pair_table (NULL for the other layouts) */
+    const void *ctab;
     int sr;                         /* stochastic rounding of the updated populations */
     uint32_t step_key;              /* the step being computed (random-bit key) */
     R rho0, dt;
@@ -129,8 +132,15 @@ void launch_aux(int store, const StepParams<R> &p, const int2 *list, int n, void
  * 2 and 3 split plain / edge kernels with register blocks of 4 x 1 and 4 x 2 nodes,
  * 4 streamed (TMA, carried moments, boundary work at the end of each unit), 5 layout 0
  * with its blocks launched in block_order, 6 the same kernel on block_desc (two nodes
- * per thread in high-order bands) */
-#define LB_NUM_VARIANTS 7
+ * per thread in high-order bands), 7 layout 0's threads with paired FP32 arithmetic on
+ * the rows without boundary work (lb_pair.cuh; FP32 and 16-bit storage), 8 layout 7
+ * with its blocks launched in block_order */
+#define LB_NUM_VARIANTS 9
+/* layout 7 / 8: p.block_order selects between them (FP32 and 16-bit storage); p.ctab
+ * must hold the tables that launch_pair_table wrote for this lattice */
+void launch_pair(int store, const StepParams<float> &p, void *stream);
+size_t pair_table_bytes();
+void launch_pair_table(const StepParams<float> &p, void *dst, void *stream);
 
 /* The quad of nodes x0 .. x0+3 of row j needs none of the boundary work of the step
  * (wall overwrite, ghost-row or ghost-column copies, pressure column, mode-B shadow or

@@ -1,0 +1,7 @@
+/* Layout-7 step kernel (paired FP32 arithmetic) instantiated for one storage format
+ * (kept in its own translation unit so the formats compile in parallel). */
+#include "lb_pair.cuh"
+
+namespace lbk {
+template void launch_pair_store<4>(const StepParams<float> &, void *);
+}

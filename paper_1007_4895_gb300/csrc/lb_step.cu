@@ -18,6 +18,8 @@ void launch_step_desc_store(const StepParams<typename Store<ST>::R> &p, int n, v
 template <int ST>
 void launch_step_split_store(const StepParams<typename Store<ST>::R> &p, int rb, const int2 *edge, int n_edge,
                              void *stream, void *edge_stream);
+template <int ST>
+void launch_pair_store(const StepParams<float> &p, void *stream);
 
 /* ---------------------------------------------------------------- mode A -- */
 
@@ -330,6 +332,17 @@ template <typename R>
 void launch_step(int store, const StepParams<R> &p, void *stream)
 {
     LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) launch_step_store<ST>(p, stream));
+}
+
+void launch_pair(int store, const StepParams<float> &p, void *stream)
+{
+    switch (store) {
+        case 1: launch_pair_store<1>(p, stream); break;
+        case 2: launch_pair_store<2>(p, stream); break;
+        case 3: launch_pair_store<3>(p, stream); break;
+        case 4: launch_pair_store<4>(p, stream); break;
+        default: break;
+    }
 }
 
 template <typename R>

@@ -132,16 +132,17 @@ def test_oscillating_wall_fp64():
     assert max(errs.values()) < F64_TOL, errs
 
 
-LAYOUTS = [0, 1, 2, 3, 4, 5, 6]
+LAYOUTS = [0, 1, 2, 3, 4, 5, 6, 7, 8]
 
 
 @pytest.mark.parametrize("variant", LAYOUTS)
 def test_every_kernel_layout_matches_oracle(variant):
     """The step-kernel layouts the autotuner chooses from (one node quad per thread,
-    TMA-fed tiles, 4 x 2 and 4 x 4 register blocks) all reproduce the oracle."""
+    TMA-fed tiles, 4 x 2 and 4 x 4 register blocks, paired FP32 arithmetic) all
+    reproduce the oracle."""
     w = ragged_workload()
     for store, tol in (("f64", F64_TOL), ("f32_dev", 1e-6), ("f32", 1e-4)):
-        if store == "f64" and variant in (1, 4):   # TMA layouts: FP32 / 16-bit storage only
+        if store == "f64" and variant in (1, 4, 7, 8):   # FP32 / 16-bit storage only
             continue
         lat, o, eff, got, ref = run_both(w, store, 60, variant=variant)
         assert lat.info()["variant"] == variant
@@ -213,14 +214,18 @@ def _col_pair(w, store, rho0_col, **kw):
     return a, b, o
 
 
+@pytest.mark.parametrize("variant", [0, 7])
 @pytest.mark.parametrize("store", ["f32_dev", "f16_dev", "bf16_dev"])
 @pytest.mark.parametrize("case", ["ragged", "pressure_channel"])
-def test_constant_per_column_reference_changes_nothing(store, case):
+def test_constant_per_column_reference_changes_nothing(store, case, variant):
     """rho0(x) = rho0 everywhere: every kernel that decodes or encodes goes through the
     per-column path with a zero shift, and the populations and moments equal those of
-    the lattice without it."""
+    the lattice without it (both lattices on one step layout)."""
+    import paper_1007_4895_gb300 as lb
     w = ragged_workload() if case == "ragged" else long_channel(nx=300, ny=37)
-    a, b, _ = _col_pair(w, store, np.full(w.nx, w.rho0))
+    a = lb.Lattice.from_workload(w, store=store, variant=variant)
+    b = lb.Lattice.from_workload(w, store=store, rho0_col=np.full(w.nx, w.rho0), variant=variant)
+    assert a.info()["variant"] == variant and b.info()["variant"] == variant
     a.step(40)
     b.step(40)
     own = a.effective_map()
@@ -400,6 +405,42 @@ def test_register_block_layouts_equal_quad_layout(store, variant):
     b.step(40)
     for s in (0, 1):
         assert np.array_equal(a.populations(s), b.populations(s)), (store, variant, s)
+
+
+@pytest.mark.parametrize("variant", [7, 8])
+@pytest.mark.parametrize("store", ["f32_dev", "f32", "f16_dev", "bf16_dev_sr", "f16_dev_sr"])
+@pytest.mark.parametrize("case", ["ragged", "pressure_channel", "bands_paper", "periodic_box"])
+def test_paired_layout_agrees_with_quad_layout(store, case, variant):
+    """Layouts 7 and 8 fold the collision into per-node coefficients, compute node pairs
+    with packed FP32 instructions and are built with multiply-add contraction, so they
+    round differently from layout 0; the update is the same (stencil, walls, shadows,
+    ghost copies, pressure columns, random bits). After 40 steps the two agree to
+    rounding: FP32 within 1e-6 of the velocity scale (deviations; 1e-5 for f itself),
+    16-bit within a few units of the stored format's last place (a rounding decision can
+    fall the other way)."""
+    import paper_1007_4895_gb300 as lb
+    rnd = "stochastic" if store.endswith("_sr") else "nearest"
+    st = store.replace("_sr", "")
+    if case == "ragged":
+        w = ragged_workload()
+    elif case == "pressure_channel":
+        w = long_channel(nx=300, ny=37)
+    elif case == "bands_paper":
+        w = couette(nx=200, ny=32, rows=4, kn=0.1, u_wall_lat=0.05, iface="paper")
+    else:
+        w = Workload(name="box", nx=260, ny=22, region_map=band_map(260, 22, 3, 0), kn_ref=0.05, gx=1e-3,
+                     walls={"bottom": {"kind": "periodic"}, "top": {"kind": "periodic"}},
+                     init=ragged_workload(nx=260, ny=22).init)
+    a = lb.Lattice.from_workload(w, store=st, variant=0, rounding=rnd)
+    b = lb.Lattice.from_workload(w, store=st, variant=variant, rounding=rnd)
+    if variant == 8 and b.info()["variant"] != 8:
+        pytest.skip("this map has no block order other than the raster order")
+    assert b.info()["variant"] == variant
+    a.step(40)
+    b.step(40)
+    errs = field_errors(b.moments(), a.moments())
+    tol = {"f32_dev": 1e-6, "f32": 1e-5, "bf16_dev": 3e-2, "f16_dev": 4e-3}[st]
+    assert errs["u"] < tol and errs["rho"] < tol, (store, case, errs)
 
 
 @pytest.mark.parametrize("store", ["f32_dev", "f32", "f16_dev"])
