@@ -1,19 +1,24 @@
 """Throughput benchmark of the multiscale lattice Boltzmann step on GB300.
 
-Workload (default): the force-driven Poiseuille channel, 1024 x 512 nodes, body force
-1e-6 (lattice units), 32 high-order (D2Q36) rows per wall and D2Q9 in the core, Kn swept
-over {0.02, 0.1, 0.5}: the three channels are advanced together, so one benchmark step
-is one time step of all three lattices (1.57 M node updates, ~156 MB of populations
-read and written, larger than the 126 MB L2). Populations are stored as FP32
-deviations from w_i rho0 and collide in FP32. Inputs are synthetic (lbinputs).
+Headline workload: the pressure-driven long microchannel, 16384 x 128 nodes, inlet /
+outlet density ratio 2, outlet Kn 0.2, region map fixed by the local-Kn threshold
+(D2Q36 bands of 10 to 19 rows per wall, D2Q9 in the core), pressure columns at both
+ends, populations stored as FP32 deviations from w_i rho0 and collided in FP32. One
+step is one time step of the whole lattice: 2.1 M node updates, about 254 MB of
+populations read and written (larger than the 126 MB L2, so no L2 flush is needed
+between steps). Inputs are synthetic (lbinputs.config3).
 
 Metric: MLUPS (million node updates per second, every node counted once per step) over
-all GPUs; the JSON line also carries the HBM roofline of the step kernel, an
-end-to-end figure through the C ABI with host-resident state, the FP64 CPU oracle
-timed on the host cores, and the same workload with FP16 / BF16 / absolute-FP32
-storage.
+all GPUs. The JSON line also carries the HBM roofline of the step, the end-to-end rate
+through the C ABI with the state resident in host memory (uploaded and read back every
+step), the FP64 CPU oracle timed on the host cores, the other storage forms on the same
+lattice with their error against the oracle, and, as a secondary key, the three
+force-driven 1024 x 512 channels.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --profile long_channel|poiseuille|stream_box [--store S] [--variant V] [--steps N]
+
+--profile only builds the named lattice and advances it N steps (for ncu).
 """
 from __future__ import annotations
 
@@ -24,7 +29,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -32,38 +36,38 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from lbinputs import config2, poiseuille  # noqa: E402
+from lbinputs import config2, config3, long_channel, poiseuille  # noqa: E402
 
 KN_SWEEP = (0.02, 0.1, 0.5)
 STORE_BYTES = {"f64": 8, "f32": 4, "f32_dev": 4, "f16_dev": 2, "bf16_dev": 2}
+ALU_OPS_PER_POP = 45   # FP32 operations per population update of the Sec. 3.1 scheme
+HEADLINE = "long channel 16384x128 (rho_in/rho_out 2, Kn_out 0.2, local-Kn map), FP32 deviation storage"
+PARITY_STEPS = 40      # steps of every storage form against the FP64 oracle on the headline lattice
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=8000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--store", default="f32_dev")
-    ap.add_argument("--no-forms", action="store_true", help="skip the other storage forms")
     ap.add_argument("--variant", type=int, default=-1, help="step-kernel layout (-1: autotune)")
+    ap.add_argument("--no-forms", action="store_true", help="skip the other storage forms")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the three-channel secondary workload")
+    ap.add_argument("--profile", default=None, choices=["long_channel", "poiseuille", "stream_box"],
+                    help="build one lattice, advance it --steps steps, exit (for ncu)")
     return ap.parse_args()
 
 
-def workloads():
-    return [config2(kn) for kn in KN_SWEEP]
-
-
-ALU_OPS_PER_POP = 45   # FP32 operations per population update (Sec. 3.1 scheme)
-
-
 def algorithmic_bytes(eff_map, sets, store):
+    """2 Q s per node: every population read once and written once per step."""
     q = np.where(eff_map == 1, sets[1], sets[0])
     return 2 * STORE_BYTES[store] * int(q.sum())
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 20 ms while the GPU is loaded."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -73,20 +77,25 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.t0 = None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
+        self.t0 = time.perf_counter()
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "20"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
+    def elapsed(self):
+        return time.perf_counter() - self.t0
+
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         self.proc.terminate()
         self.proc.wait()
         sm, smax, reasons = [], [], set()
@@ -117,47 +126,31 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def form_accuracy(lb, forms):
-    """Relative velocity error (max over nodes, C18) of each storage form against the
-    FP64 oracle on a steady force-driven channel (4 x 64, Kn 0.1, 32-row-per-wall
-    equivalent band of 10 rows, 6000 steps): the accuracy behind each form's throughput."""
-    import oracle
-    from lbinputs import poiseuille
-    w = poiseuille(nx=4, ny=64, rows=10, kn=0.1, g_lat=1e-5)
-    steps = 6000
-    out, ref = {}, None
-    for name, (store, rnd) in forms.items():
-        lat = lb.Lattice.from_workload(w, store=store, rounding=rnd, variant=0)
-        if ref is None:
-            o = oracle.Oracle(w.nx, w.ny, lat.effective_map(), kn_ref=w.kn_ref, gx=w.gx, walls=w.walls, dt=lat.dt,
-                              h=lat.h)
-            o.init_equilibrium(1.0, 0.0, 0.0)
-            o.step(steps)
-            ref = o.moments()
-        lat.step(steps)
-        m = lat.moments(mask=0b111)
-        du = np.sqrt((m["ux"] - ref["ux"]) ** 2 + (m["uy"] - ref["uy"]) ** 2)
-        out[name] = float(du.max() / np.sqrt(ref["ux"] ** 2 + ref["uy"] ** 2).max())
-        lat.close()
-    return out
+def kernel_sha():
+    import hashlib
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_1007_4895_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:12]
 
 
-def cpu_baseline(seconds=12.0):
-    """The FP64 oracle on one full-size channel of the sweep (Kn = 0.1), all host cores."""
-    import oracle
-    w = config2(0.1)
-    o = oracle.Oracle(w.nx, w.ny, w.region_map, kn_ref=w.kn_ref, gx=w.gx, walls=w.walls)
-    o.init_equilibrium(1.0, 0.0, 0.0)
-    o.step(1)
-    n, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < seconds or n < 2:
-        o.step(1)
-        n += 1
-    dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
-    return {"value": w.cells * n / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"one 1024x512 channel (Kn 0.1) of the sweep, {n} steps, {dt:.1f} s, FP64, OpenMP"}
+def stored_traffic(workload, store, variant):
+    """DRAM bytes per step from the committed ncu capture, when it was taken on the
+    current kernel sources, this workload, storage and layout; else None."""
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        tj = json.load(open(tp))
+    except Exception:
+        return None
+    for e in tj.get("captures", []):
+        if (e.get("workload") == workload and e.get("store") == store and e.get("variant") == variant
+                and e.get("kernel_sha") == kernel_sha()):
+            return e.get("bytes_per_step")
+    return None
 
+
+# ------------------------------------------------------------- timing helpers
 
 def max_over_ranks(torch, dist, ms, device):
     """The job's time: the slowest rank's (every rank gets it). Without a process group,
@@ -175,54 +168,9 @@ def job_mlups(world, cells_per_rank, steps, ms):
     return world * cells_per_rank * steps / (ms / 1e3) / 1e6
 
 
-def run_reference(args, rank):
-    """The oracle as the reference arm: each step advances a 64-column slab of each of
-    the three channels (the flow is x-invariant, so a slab is the same problem)."""
-    if rank != 0:
-        return
-    import oracle
-    labs = []
-    for kn in KN_SWEEP:
-        w = poiseuille(nx=64, ny=512, rows=32, kn=kn)
-        o = oracle.Oracle(w.nx, w.ny, w.region_map, kn_ref=w.kn_ref, gx=w.gx, walls=w.walls)
-        o.init_equilibrium(1.0, 0.0, 0.0)
-        labs.append((w, o))
-    for _ in range(args.warmup):
-        for _, o in labs:
-            o.step(1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for _, o in labs:
-            o.step(1)
-    dt = time.perf_counter() - t0
-    cells = sum(w.cells for w, _ in labs)
-    value = cells * args.steps / dt / 1e6
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
-    line = {
-        "impl": "reference", "metric": "coupled-LB MLUPS", "value": value, "unit": "MLUPS",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "poiseuille 1024x512 x3 (Kn 0.02/0.1/0.5), D2Q9 core + D2Q36 32 rows/wall",
-                   "sample": "64-column slab of each channel per step"},
-        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                         "sample": f"64x512 slab of each of the 3 channels, {args.steps} steps"},
-        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
-
-
-def channel_lattices(lb, torch, store, variant=-1, rounding="nearest"):
-    """The channels of the workload, each on its own CUDA stream (independent problems,
-    as a user would run them: one channel's tail overlaps the next one's launch)."""
-    streams = [torch.cuda.Stream() for _ in workloads()]
-    lats = [lb.Lattice.from_workload(w, store=store, variant=variant, rounding=rounding, stream=s)
-            for w, s in zip(workloads(), streams)]
-    return lats, streams
-
-
 def timed_steps(torch, lats, streams, steps):
-    """CUDA events around `steps` steps of every channel: the start event on the current
-    stream is waited for by every channel stream, and the stop event follows all of
+    """CUDA events around `steps` steps of every lattice: the start event on the current
+    stream is waited for by every lattice's stream, and the stop event follows all of
     them. Returns milliseconds."""
     main = torch.cuda.current_stream()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -241,10 +189,10 @@ def timed_steps(torch, lats, streams, steps):
     return start.elapsed_time(stop)
 
 
-def launch_times(torch, lats, streams, reps):
-    """Per-launch durations of the step kernel, one launch at a time: events on the
-    launching stream, each launch ordered after the previous one's end event so that
-    nothing overlaps and no host gap falls inside a measurement."""
+def step_times(torch, lats, streams, reps):
+    """Duration of one step of each lattice, one at a time: events on the lattice's own
+    stream, each step ordered after the previous one's end event, so that nothing
+    overlaps and no host gap falls inside a measurement."""
     ev, prev = [], None
     for _ in range(reps):
         for i, (lat, s) in enumerate(zip(lats, streams)):
@@ -260,24 +208,129 @@ def launch_times(torch, lats, streams, reps):
     return [(i, a.elapsed_time(b)) for i, a, b in ev]
 
 
-def time_form(lb, torch, store, steps, warmup, variant=-1, with_kernel_times=True, rounding="nearest"):
-    lats, streams = channel_lattices(lb, torch, store, variant, rounding)
-    for _ in range(warmup):
-        for lat in lats:
-            lat.step(1)
-    torch.cuda.synchronize()
-    total_ms = timed_steps(torch, lats, streams, steps)
-    kern = [t for _, t in launch_times(torch, lats, streams, 20)] if with_kernel_times else []
-    info = [lat.info() for lat in lats]
-    eff = [lat.effective_map() for lat in lats]
-    nbytes = [algorithmic_bytes(e, lat.sets, store) for e, lat in zip(eff, lats)]
-    for lat in lats:
-        lat.close()
-    return total_ms, kern, nbytes, info
+def launches_per_step(variant, pressure):
+    """Kernels one lattice step launches: the step kernel, the edge-list kernel of the
+    split layouts (2, 3; the list always holds the wall rows), and the pressure pass when
+    the lattice has pressure columns."""
+    return (2 if variant in (2, 3) else 1) + (1 if pressure else 0)
 
+
+# ------------------------------------------------------------- oracle parts
+
+def cpu_baseline(seconds=12.0):
+    """The FP64 oracle on the headline lattice, all host cores, for about `seconds`."""
+    import oracle
+    w = config3()
+    o = oracle.Oracle(w.nx, w.ny, w.region_map, kn_ref=w.kn_ref, rho_ref=w.rho_ref, walls=w.walls, cfl=w.cfl)
+    o.init_equilibrium(*w.init)
+    o.step(1)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds or n < 2:
+        o.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    return {"value": w.cells * n / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"the 16384x128 long channel, {n} steps, {dt:.1f} s, FP64, OpenMP"}
+
+
+def oracle_reference_fields(steps, lat):
+    """The FP64 oracle's moments of the headline lattice after `steps` steps, on the map
+    the GPU lattice runs (tile-quantised) with its time step and spacing."""
+    import oracle
+    w = config3()
+    o = oracle.Oracle(w.nx, w.ny, lat.effective_map(), kn_ref=w.kn_ref, rho_ref=w.rho_ref, walls=w.walls,
+                      dt=lat.dt, h=lat.h)
+    o.init_equilibrium(*w.init)
+    o.step(steps)
+    return o.moments()
+
+
+def field_error(got, ref):
+    """Max relative errors: velocity (vector norm) by max |u_ref|, density by max rho."""
+    du = np.sqrt((got["ux"] - ref["ux"]) ** 2 + (got["uy"] - ref["uy"]) ** 2)
+    e_u = float(du.max() / np.sqrt(ref["ux"] ** 2 + ref["uy"] ** 2).max())
+    e_rho = float(np.abs(got["rho"] - ref["rho"]).max() / np.abs(ref["rho"]).max())
+    return e_u, e_rho
+
+
+def steady_accuracy(lb, forms):
+    """Relative velocity error (max over nodes) of each storage form against the FP64
+    oracle on a steady force-driven channel (4 x 64, Kn 0.1, 10 high-order rows per wall,
+    6000 steps): the long-run accuracy behind each form."""
+    import oracle
+    w = poiseuille(nx=4, ny=64, rows=10, kn=0.1, g_lat=1e-5)
+    steps = 6000
+    out, ref = {}, None
+    for name, (store, rnd) in forms.items():
+        lat = lb.Lattice.from_workload(w, store=store, rounding=rnd)
+        if ref is None:
+            o = oracle.Oracle(w.nx, w.ny, lat.effective_map(), kn_ref=w.kn_ref, gx=w.gx, walls=w.walls, dt=lat.dt,
+                              h=lat.h)
+            o.init_equilibrium(1.0, 0.0, 0.0)
+            o.step(steps)
+            ref = o.moments()
+        lat.step(steps)
+        out[name] = field_error(lat.moments(mask=0b111), ref)[0]
+        lat.close()
+    return out
+
+
+def run_reference(args, rank):
+    """The oracle as the reference arm: each step advances a 512-column long channel of
+    the headline's height, density ratio, Kn and map rule (a bounded sample of the
+    headline lattice, with its per-node cost), on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    w = long_channel(nx=512, ny=128)
+    o = oracle.Oracle(w.nx, w.ny, w.region_map, kn_ref=w.kn_ref, rho_ref=w.rho_ref, walls=w.walls, cfl=w.cfl)
+    o.init_equilibrium(*w.init)
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    value = w.cells * args.steps / dt / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    line = {
+        "impl": "reference", "metric": "coupled-LB MLUPS", "value": value, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": HEADLINE, "sample": "512x128 long channel of the same density ratio, Kn and map rule per step"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"512x128 long channel, {args.steps} steps"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- profiling mode
+
+def profile_only(args):
+    import torch
+
+    import paper_1007_4895_gb300 as lb
+    if args.profile == "stream_box":
+        periodic = {s: {"kind": "periodic"} for s in ("bottom", "top", "left", "right")}
+        lat = lb.Lattice(2048, 1024, np.zeros((1024, 2048), np.uint8), kn_ref=0.002, rho_ref=1.0, walls=periodic,
+                         store=args.store, scheme="stream")
+    else:
+        w = config3() if args.profile == "long_channel" else config2(0.1)
+        lat = lb.Lattice.from_workload(w, store=args.store, variant=args.variant)
+    lat.step(args.steps)
+    torch.cuda.synchronize()
+    print(args.profile, args.store, lat.info())
+
+
+# ------------------------------------------------------------- the benchmark
 
 def main():
     args = parse()
+    if args.profile:
+        profile_only(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -286,6 +339,7 @@ def main():
         return
 
     import torch
+
     import paper_1007_4895_gb300 as lb
     torch.cuda.set_device(local)
     dist = None
@@ -298,118 +352,139 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    cells = sum(w.cells for w in workloads())
-    # main timed region: K steps of the three channels on this GPU, each channel on its
-    # own stream
-    lats, streams = channel_lattices(lb, torch, args.store, args.variant)
+    # headline: K steps of the long channel on this GPU (one replica per rank)
+    w = config3()
+    stream = torch.cuda.Stream()
+    lat = lb.Lattice.from_workload(w, store=args.store, variant=args.variant, stream=stream)
     for _ in range(args.warmup):
-        for lat in lats:
-            lat.step(1)
+        lat.step(1)
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    ms = timed_steps(torch, lats, streams, args.steps)
+    ms = timed_steps(torch, [lat], [stream], args.steps)
+    # keep the GPU loaded (untimed) until the clock sampler has seen a second of it
+    while clocks.elapsed() < 1.0:
+        for _ in range(200):
+            lat.step(1)
+        torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
     ms = max_over_ranks(torch, dist, ms, "cuda")
-    value = job_mlups(world, cells, args.steps, ms)
-    variants = [lat.info()["variant"] for lat in lats]
-    eff = [lat.effective_map() for lat in lats]
-    nbytes = [algorithmic_bytes(e, lat.sets, args.store) for e, lat in zip(eff, lats)]
+    value = job_mlups(world, w.cells, args.steps, ms)
+    variant = lat.info()["variant"]
+    nbytes = algorithmic_bytes(lat.effective_map(), lat.sets, args.store)
 
-    # per-launch durations of the step kernel, on the stream it is launched on
-    kt = launch_times(torch, lats, streams, max(3, min(60, args.steps // 50)))
-    avg_ms = statistics.mean(t for _, t in kt)
-    avg_bytes = statistics.mean(nbytes[i] for i, _ in kt)
+    # roofline of the step (step kernel + pressure pass), one step at a time
+    st = [t for _, t in step_times(torch, [lat], [stream], 60)]
+    step_ms = statistics.mean(st)
     peak, peak_src = measured_peak_hbm()
-    achieved = avg_bytes / (avg_ms / 1e3) / 1e9
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tp):
-        try:
-            tj = json.load(open(tp))
-            if tj.get("store") == args.store and tj.get("kernel_sha") == kernel_sha():
-                traffic = tj.get("bytes_per_launch")
-        except Exception:
-            traffic = None
-    # the same launches against the FP32 ALU: 45 operations per population update (moments
-    # 3, equilibrium and force 8, four limited fluxes 28, update 6), peak = SMs x 128 FP32
-    # lanes x the SM clock sampled during the timed region
-    pops = [algorithmic_bytes(e, lat.sets, args.store) // (2 * STORE_BYTES[args.store]) for e, lat in zip(eff, lats)]
-    avg_pops = statistics.mean(pops[i] for i, _ in kt)
+    achieved = nbytes / (step_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": stored_traffic("long_channel", args.store, variant),
+                "kernel": "lbk step kernel + pressure pass (one step of the long channel)",
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, copy burst)",
+                "algorithmic_bytes_per_launch": nbytes, "launch_ms": step_ms,
+                "launches": "one step at a time (isolated)"}
+    pops = nbytes // (2 * STORE_BYTES[args.store])
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
     alu_peak = nsm * 128 * sm_mhz * 1e6 / 1e9
-    alu_achieved = ALU_OPS_PER_POP * avg_pops / (avg_ms / 1e3) / 1e9
+    alu_achieved = ALU_OPS_PER_POP * pops / (step_ms / 1e3) / 1e9
     roofline_alu = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Gop/s",
                     "frac": alu_achieved / alu_peak, "ops_per_population": ALU_OPS_PER_POP,
                     "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (sampled)"}
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "lbk::step kernel (one launch per channel per step)",
-                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, copy burst)",
-                "algorithmic_bytes_per_launch": avg_bytes, "launch_ms": avg_ms,
-                "launches": "one at a time (isolated kernel durations)",
-                "whole_job_frac": sum(nbytes) * args.steps / (ms / 1e3) / 1e9 / peak}
 
-    # end to end through the C ABI with host-resident state: per step, each channel's
-    # state comes in from pinned host memory and its mass / residual goes back
-    e2e_steps = max(5, min(100, args.steps // 20))
-    nbs = [lat.state_bytes() for lat in lats]
-    host = [torch.empty(n, dtype=torch.uint8, pin_memory=True) for n in nbs]
-    for lat, hbuf in zip(lats, host):
-        lb.lb_state_store(lat.ctx, hbuf.data_ptr(), hbuf.numel())
+    # end to end through the C ABI with the state in host memory: every step uploads the
+    # compact state from pinned host memory, steps, and reads the new state back
+    e2e_steps = max(5, min(50, args.steps // 100))
+    nb = lat.state_bytes()
+    host = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+    lb.lb_state_store(lat.ctx, host.data_ptr(), nb)
     barrier()
     t0 = time.perf_counter()
-    # each channel reads its previous step's result just before uploading its next
-    # state, so one channel's upload overlaps the other channels' steps
-    for k in range(e2e_steps):
-        for lat, hbuf in zip(lats, host):
-            if k > 0:
-                lat.reductions()
-            lb.lb_state_load(lat.ctx, hbuf.data_ptr(), hbuf.numel())
-            lat.step(1)
-    for lat in lats:
-        lat.reductions()
+    for _ in range(e2e_steps):
+        lb.lb_state_load(lat.ctx, host.data_ptr(), nb)
+        lat.step(1)
+        lb.lb_state_store(lat.ctx, host.data_ptr(), nb)   # synchronous: the host holds the new state
     barrier()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * cells * e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
-           "h2d_bytes_per_step": int(sum(nbs)), "d2h_bytes_per_step": (4 * 8 + 4) * len(lats),
-           "steps": e2e_steps}
-    for lat in lats:
-        lat.close()
+    e2e = {"value": world * w.cells * e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": int(nb), "d2h_bytes_per_step": int(nb), "steps": e2e_steps,
+           "what": "compact state (own-set populations) uploaded, one step, state read back"}
+    lat.close()
 
+    # the other storage forms on the headline lattice: rate, roofline, error against the
+    # FP64 oracle after PARITY_STEPS steps from the same start
     forms = {}
-    if not args.no_forms:
-        variants_of_forms = {"f32": ("f32", "nearest"), "f16_dev": ("f16_dev", "nearest"),
-                             "bf16_dev": ("bf16_dev", "nearest"), "f16_dev_sr": ("f16_dev", "stochastic"),
-                             "bf16_dev_sr": ("bf16_dev", "stochastic")}
-        for name, (store, rnd) in variants_of_forms.items():
-            fs = max(50, min(args.steps, 1000))
-            tot, kern, nb, info = time_form(lb, torch, store, fs, 5, args.variant, rounding=rnd)
-            km = statistics.mean(kern)
-            forms[name] = {"value": cells * fs / (tot / 1e3) / 1e6, "unit": "MLUPS",
-                           "roofline_frac": (statistics.mean(nb) / (km / 1e3) / 1e9) / peak,
-                           "variant": info[0]["variant"], "rounding": rnd}
-        acc = form_accuracy(lb, dict({"f32_dev": ("f32_dev", "nearest")}, **variants_of_forms))
+    if not args.no_forms and rank == 0:
+        specs = {"f32_dev": ("f32_dev", "nearest"), "f32": ("f32", "nearest"), "f16_dev": ("f16_dev", "nearest"),
+                 "bf16_dev": ("bf16_dev", "nearest"), "f16_dev_sr": ("f16_dev", "stochastic"),
+                 "bf16_dev_sr": ("bf16_dev", "stochastic")}
+        ref = None
+        for name, (store, rnd) in specs.items():
+            f = lb.Lattice.from_workload(w, store=store, rounding=rnd)
+            if ref is None:
+                ref = oracle_reference_fields(PARITY_STEPS, f)
+            f.step(PARITY_STEPS)
+            e_u, e_rho = field_error(f.moments(mask=0b111), ref)
+            s2 = torch.cuda.current_stream()
+            for _ in range(5):
+                f.step(1)
+            t = statistics.mean(x for _, x in step_times(torch, [f], [s2], 30))
+            fb = algorithmic_bytes(f.effective_map(), f.sets, store)
+            forms[name] = {"value": w.cells / (t / 1e3) / 1e6, "unit": "MLUPS",
+                           "roofline_frac": fb / (t / 1e3) / 1e9 / peak, "variant": f.info()["variant"],
+                           "rounding": rnd, f"e_u_vs_fp64_oracle_{PARITY_STEPS}_steps": e_u,
+                           f"e_rho_vs_fp64_oracle_{PARITY_STEPS}_steps": e_rho}
+            f.close()
+        acc = steady_accuracy(lb, specs)
         for name, e in acc.items():
-            forms.setdefault(name, {})["e_u_vs_fp64_oracle"] = e
-        forms["accuracy_case"] = "steady Poiseuille 4x64, Kn 0.1, 6000 steps, max relative velocity error"
+            forms[name]["e_u_steady_poiseuille_6000_steps"] = e
+        forms["accuracy_cases"] = (f"the headline lattice after {PARITY_STEPS} steps against the FP64 oracle; "
+                                   "steady Poiseuille 4x64, Kn 0.1, 6000 steps; max relative errors")
+
+    # secondary: three force-driven 1024 x 512 channels (Kn 0.02 / 0.1 / 0.5), one stream
+    # each, stepped together
+    secondary = None
+    if not args.no_secondary:
+        streams = [torch.cuda.Stream() for _ in KN_SWEEP]
+        lats = [lb.Lattice.from_workload(config2(kn), store=args.store, variant=args.variant, stream=s)
+                for kn, s in zip(KN_SWEEP, streams)]
+        for _ in range(10):
+            for x in lats:
+                x.step(1)
+        torch.cuda.synchronize()
+        k2 = max(100, min(args.steps, 3000))
+        ms2 = timed_steps(torch, lats, streams, k2)
+        cells2 = sum(x.nx * x.ny for x in lats)
+        nb2 = [algorithmic_bytes(x.effective_map(), x.sets, args.store) for x in lats]
+        kt = step_times(torch, lats, streams, 20)
+        one = statistics.mean(t for _, t in kt)
+        secondary = {"workload": "poiseuille 1024x512 x3 (Kn 0.02/0.1/0.5), D2Q9 core + D2Q36 32 rows/wall, "
+                                 "body force 1e-6 lattice",
+                     "value": cells2 * k2 / (ms2 / 1e3) / 1e6, "unit": "MLUPS", "steps": k2,
+                     "whole_job_frac": sum(nb2) * k2 / (ms2 / 1e3) / 1e9 / peak,
+                     "one_channel_step_ms": one,
+                     "one_channel_frac": statistics.mean(nb2) / (one / 1e3) / 1e9 / peak,
+                     "variants": [x.info()["variant"] for x in lats],
+                     "l2": "per channel launch 51.9 MB < L2: its writes stay in L2 within a launch"}
+        for x in lats:
+            x.close()
 
     line = {
         "metric": "coupled-LB MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "poiseuille 1024x512 x3 (Kn 0.02/0.1/0.5), D2Q9 core + D2Q36 32 rows/wall, "
-                               "body force 1e-6 lattice, FP32 deviation storage",
-                   "global_batch": 3 * world, "cells_per_gpu": cells, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (156 MB of populations touched per step)",
-                   "kernel_variants": variants},
+        "config": {"workload": HEADLINE, "cells_per_gpu": w.cells, "parallelism": f"replicas x{world}",
+                   "l2": f"inputs larger than L2 ({nbytes / 1e6:.0f} MB of populations read and written per step)",
+                   "kernel_variant": variant},
         "roofline": roofline,
         "roofline_alu": roofline_alu,
         "e2e": e2e,
         "clocks": clk,
-        "gpu_launches": args.steps * sum(launches_per_step(v) for v in variants),
+        "gpu_launches": args.steps * launches_per_step(variant, pressure=True),
         "forms": forms,
+        "secondary": secondary,
     }
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline()
@@ -417,21 +492,6 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
-
-
-def launches_per_step(variant):
-    """Kernels one lattice step launches on the benchmark workload (periodic x, no
-    pressure columns, mode-B interfaces): the step kernel, plus the edge-list kernel of
-    the split layouts (2, 3), whose list is never empty here (wall rows)."""
-    return 2 if variant in (2, 3) else 1
-
-
-def kernel_sha():
-    import hashlib
-    h = hashlib.sha1()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1007_4895_gb300", "csrc"))):
-        h.update(open(os.path.join(ROOT, "paper_1007_4895_gb300", "csrc", f), "rb").read())
-    return h.hexdigest()[:12]
 
 
 if __name__ == "__main__":
