@@ -25,6 +25,15 @@ _lock = threading.Lock()
 _lib = None
 
 SIDES = ("bottom", "top", "left", "right")
+# storage models of the oracle (set_storage): the formats of the GPU path's lb_opts.store
+# and lb_opts.rounding
+STORAGE_MODES = {"exact": 0, "f32": 1, "f32_dev": 2, "f16_dev": 3, "bf16_dev": 4, "f16_dev_sr": 5, "bf16_dev_sr": 6}
+
+
+def store_round(mode: str, d: float, bits: int = 0, set_value: bool = False) -> float:
+    """One deviation through a storage model's rounding (bits: the 32 random bits of a
+    stochastic mode)."""
+    return lib().or_store_round(STORAGE_MODES[mode], float(d), int(bits) & 0xffffffff, 1 if set_value else 0)
 WALL_KIND = {"periodic": 0, "diffuse": 1, "pressure": 2}
 
 
@@ -75,6 +84,9 @@ def lib():
             L.or_get_populations.argtypes = [ctypes.c_void_p, ctypes.c_int, dp]
             L.or_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
             L.or_moments.argtypes = [ctypes.c_void_p, dp]
+            L.or_set_storage.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, dp]
+            L.or_store_round.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_uint32, ctypes.c_int]
+            L.or_store_round.restype = ctypes.c_double
             L.or_time.argtypes = [ctypes.c_void_p]
             L.or_time.restype = ctypes.c_double
             _lib = L
@@ -178,6 +190,16 @@ class Oracle:
         out = np.zeros((self.q[s], self.ny, self.nx))
         lib().or_get_populations(self._p, s, _dp(out))
         return out
+
+    def set_storage(self, mode: str, rho0: float = 1.0, rho0_col=None):
+        """Round the stored populations of every evolved node after each update the way
+        a storage format holds them (STORAGE_MODES); "exact" turns it off."""
+        col = None
+        if rho0_col is not None:
+            self._rho_r = np.ascontiguousarray(np.asarray(rho0_col, dtype=np.float64).reshape(self.nx))
+            col = _dp(self._rho_r)
+        if lib().or_set_storage(self._p, STORAGE_MODES[mode], float(rho0), col) != 0:
+            raise ValueError(mode)
 
     def step(self, n: int = 1):
         lib().or_step(self._p, int(n))

@@ -40,6 +40,10 @@
  *   - Pressure columns (x = 0, x = nx-1, interior rows): f = f_eq(rho_b, u_1)
  *     + [f - f_eq](node 1 step inwards), the same virtual-boundary construction
  *     as Sec. 2.2; ghosts beyond them are copies.
+ *
+ * A storage model (or_set_storage, off by default) rounds the stored populations of
+ * every evolved node after each update the way a finite-precision storage format does,
+ * so that the error a format adds can be computed here, in FP64 otherwise.
  */
 #include <math.h>
 #include <stdint.h>
@@ -235,6 +239,20 @@ typedef struct {
     double wall_ux[4], wall_uy[4], wall_rho[4], wall_omega[4];
 } or_cfg;
 
+/* Storage model (a test switch, off by default): after each update the populations of
+ * an evolved node are stored the way a finite-precision format holds them, so that the
+ * error a storage format adds to the method can be computed in FP64 and compared with
+ * what a finite-precision implementation shows. */
+enum {
+    ST_EXACT = 0,        /* no rounding (the oracle proper) */
+    ST_F32 = 1,          /* f itself rounded to FP32 */
+    ST_F32_DEV = 2,      /* the deviation f / w - rho_r rounded to FP32 */
+    ST_F16_DEV = 3,      /* ... to FP16, to nearest */
+    ST_BF16_DEV = 4,     /* ... to BF16, to nearest */
+    ST_F16_DEV_SR = 5,   /* ... to FP16, stochastically */
+    ST_BF16_DEV_SR = 6   /* ... to BF16, stochastically */
+};
+
 typedef struct {
     or_cfg c;
     or_vset set[2];
@@ -243,6 +261,8 @@ typedef struct {
     double *fn[2];
     double t;
     int64_t step;
+    int32_t store;               /* storage model, ST_* */
+    double *rho_r;               /* [nx]: reference density of each column's deviation */
 } or_lattice;
 
 #define F(L, s, a, i, j) ((L)->f[s][((size_t)(a) * (L)->c.ny + (size_t)(j)) * (L)->c.nx + (size_t)(i)])
@@ -411,6 +431,91 @@ static int is_evolved(const or_lattice *L, int i, int j)
     return !is_pressure_node(L, i, j) && !is_iface_node(L, i, j);
 }
 
+/* ------------------------------------------------------- storage model -- */
+
+/* C. Wellons' "lowbias32" integer hash (xorshift-multiply finaliser, published 2018):
+ * the counter-based source of the stochastic-rounding bits. The key of one stored value
+ * names the node, the population and the step that produces it. */
+static uint32_t lowbias32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+static uint32_t round_key(int i, int j, int nx, int a, uint32_t step)
+{
+    return lowbias32(lowbias32((uint32_t)j * (uint32_t)nx + (uint32_t)i) ^ lowbias32(((uint32_t)a << 24) ^ step));
+}
+
+static float f32_of_bits(uint32_t b) { float f; memcpy(&f, &b, 4); return f; }
+static uint32_t bits_of_f32(float f) { uint32_t b; memcpy(&b, &f, 4); return b; }
+
+/* BF16 = the upper 16 bits of FP32. Nearest (ties to even) by adding half an ulp of the
+ * kept part, or stochastically by adding 16 random bits: the kept part then rounds up
+ * with probability equal to the dropped fraction of its magnitude. */
+static double bf16_round(float v, int stochastic, uint32_t r)
+{
+    uint32_t b = bits_of_f32(v);
+    if ((b & 0x7f800000u) == 0x7f800000u) return v;
+    if (stochastic) b += r & 0xffffu;
+    else b += 0x7fffu + ((b >> 16) & 1u);
+    return f32_of_bits(b & 0xffff0000u);
+}
+
+/* FP16: nearest (ties to even), or stochastically between the two codes that bracket
+ * v: the one further from zero with probability (v - lo) / (hi - lo), lo the code
+ * towards zero; a 24-bit uniform from the key's upper bits. */
+static double f16_round(float v, int stochastic, uint32_t r)
+{
+    _Float16 h = (_Float16)v;
+    if (!stochastic || !(fabsf(v) < 65504.0f) || (float)h == v) return (double)(float)h;
+    /* lo: the code next to v towards zero */
+    _Float16 lo = h;
+    if (fabsf((float)h) > fabsf(v)) {
+        uint16_t hb;
+        memcpy(&hb, &h, 2);
+        hb = (uint16_t)(hb - 1u);
+        memcpy(&lo, &hb, 2);
+    }
+    uint16_t lb;
+    memcpy(&lb, &lo, 2);
+    uint16_t ub = (uint16_t)(lb + 1u);
+    _Float16 hi;
+    memcpy(&hi, &ub, 2);
+    float lof = (float)lo, hif = (float)hi;
+    float frac = (v - lof) / (hif - lof);
+    float u = (float)(r >> 8) * (1.0f / 16777216.0f);
+    return (double)(u < frac ? hif : lof);
+}
+
+/* One stored value of population a at node (i, j): f -> the format -> f. `set_value`:
+ * a value the wall sets (rounded to nearest, as every value that is not an update of
+ * the population's own previous value). */
+double or_store_round(int mode, double d, uint32_t bits, int set_value)
+{
+    switch (mode) {
+        case ST_F32_DEV: return (double)(float)d;
+        case ST_F16_DEV: return f16_round((float)d, 0, 0);
+        case ST_BF16_DEV: return bf16_round((float)d, 0, 0);
+        case ST_F16_DEV_SR: return f16_round((float)d, !set_value, bits);
+        case ST_BF16_DEV_SR: return bf16_round((float)d, !set_value, bits);
+        default: return d;
+    }
+}
+
+static double stored(const or_lattice *L, int s, int a, int i, int j, double f, int set_value)
+{
+    if (L->store == ST_EXACT) return f;
+    if (L->store == ST_F32) return (double)(float)f;
+    const double w = L->set[s].w[a], r = L->rho_r[i];
+    const uint32_t key = round_key(i, j, L->c.nx, a, (uint32_t)(L->step + 1));
+    return w * (r + or_store_round(L->store, f / w - r, key, set_value));
+}
+
 /* One node: Sec. 3.1 update of every population of its set, then the Sec. 3.2 wall
  * overwrite when the node lies on a diffuse wall. */
 static void update_node(or_lattice *L, int i, int j)
@@ -438,7 +543,7 @@ static void update_node(or_lattice *L, int i, int j)
                 + (dt / tau) * (feq(vs, a, rho, ux, uy) - f0)
                 + force(vs, a, rho, ux, uy, L->c.gx, L->c.gy) * dt;
     }
-    int side = -1;
+    int side = -1, set_by_wall[OR_QMAX] = {0};
     if (j == 0 && L->c.wall_kind[SIDE_BOTTOM] == W_DIFFUSE) side = SIDE_BOTTOM;
     if (j == L->c.ny - 1 && L->c.wall_kind[SIDE_TOP] == W_DIFFUSE) side = SIDE_TOP;
     if (side >= 0) {
@@ -453,9 +558,12 @@ static void update_node(or_lattice *L, int i, int j)
         }
         double rho_w = num / den;
         for (int a = 0; a < vs->q; ++a)
-            if (vs->cy[a] * ny_ > 0.0) fnew[a] = rho_w * feq(vs, a, 1.0, uwx, uwy);
+            if (vs->cy[a] * ny_ > 0.0) {
+                fnew[a] = rho_w * feq(vs, a, 1.0, uwx, uwy);
+                set_by_wall[a] = 1;
+            }
     }
-    for (int a = 0; a < vs->q; ++a) FN(L, s, a, i, j) = fnew[a];
+    for (int a = 0; a < vs->q; ++a) FN(L, s, a, i, j) = stored(L, s, a, i, j, fnew[a], set_by_wall[a]);
 }
 
 /* ------------------------------------------------------------- public API -- */
@@ -470,6 +578,8 @@ or_lattice *or_create(const or_cfg *cfg, const uint8_t *map)
         return NULL;
     }
     size_t cells = (size_t)cfg->nx * (size_t)cfg->ny;
+    L->store = ST_EXACT;
+    L->rho_r = (double *)calloc((size_t)cfg->nx, sizeof(double));
     L->map = (uint8_t *)malloc(cells);
     memcpy(L->map, map, cells);
     for (int s = 0; s < 2; ++s) {
@@ -483,6 +593,7 @@ void or_destroy(or_lattice *L)
 {
     if (!L) return;
     for (int s = 0; s < 2; ++s) { free(L->f[s]); free(L->fn[s]); }
+    free(L->rho_r);
     free(L->map);
     free(L);
 }
@@ -516,6 +627,16 @@ void or_get_populations(const or_lattice *L, int s, double *dst)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i)
                 dst[((size_t)a * ny + j) * nx + i] = in_set_value(L, s, a, i, j);
+}
+
+/* Storage model for the following steps (ST_*), with the reference density of each
+ * column's deviation (rho_r[nx]; NULL: rho0 everywhere). */
+int or_set_storage(or_lattice *L, int mode, double rho0, const double *rho_r)
+{
+    if (mode < ST_EXACT || mode > ST_BF16_DEV_SR) return -1;
+    L->store = mode;
+    for (int i = 0; i < L->c.nx; ++i) L->rho_r[i] = rho_r ? rho_r[i] : rho0;
+    return 0;
 }
 
 void or_step(or_lattice *L, int64_t n)
