@@ -276,6 +276,89 @@ def steady_accuracy(lb, forms):
     return out
 
 
+def config5_study(lb, torch, nx=16384, ny=128, steps=2000, every=200, samples=100000, threshold=3e-4, epochs=20):
+    """Learned interface placement on the long channel (the headline geometry at CFL 0.38,
+    where an all-high-order map is stable): an all-D2Q36 run gives the features and the
+    labels (beyond-second-order residual e3 > threshold) of `samples` nodes drawn with the
+    same count from every wall distance; the network trains on the GPU; a run from the
+    fixed local-Kn map then has its map updated by the network every `every` steps. The
+    three maps (fixed, learned, all-D2Q36) are compared on velocity error against the
+    all-D2Q36 run after `steps` steps, on their high-order fraction and on MLUPS (timed
+    with their map updates), and the cost of one map update is timed."""
+    from lbinputs import mlp_init, wall_stratified_sample
+    w = long_channel(nx=nx, ny=ny, cfl=0.38)
+    n = nx * ny
+    allh = lb.Lattice(nx, ny, np.ones((ny, nx), np.uint8), sets=w.sets, kn_ref=w.kn_ref, rho_ref=w.rho_ref,
+                      walls=w.walls, store="f32_dev", rho0=w.rho0, cfl=w.cfl)
+    allh.init_equilibrium(*w.init)
+    allh.step(steps)
+    ref = allh.moments(mask=0b111)
+    F = torch.empty((8, ny, nx), device="cuda")
+    E = torch.empty((ny, nx), device="cuda")
+    allh.features_into(F)
+    allh.hermite_residual_into(E)
+    idx = torch.tensor(wall_stratified_sample(ny, nx, samples), device="cuda", dtype=torch.long)
+    X = F.reshape(8, n)[:, idx].contiguous()
+    Y = (E.reshape(n)[idx] > threshold).float().contiguous()
+    Xh = X.cpu().numpy()
+    norm = np.concatenate([Xh.mean(1), Xh.std(1) + 1e-12]).astype(np.float32)
+    net = lb.MLP(mlp_init(1007), norm)
+    loss0 = net.grad(X, Y)[1]
+    t0 = time.perf_counter()
+    loss = net.train(X, Y, epochs=epochs, batch=256, lr=1e-3, seed=1007)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    pX = torch.empty(samples, device="cuda")
+    net.infer(X, pX)
+    acc = float(((pX > 0.5).float() == Y).float().mean())
+    label_share = float(Y.mean())
+    # inference over the whole lattice, CUDA events
+    P = torch.empty(n, device="cuda")
+    Fn = F.reshape(8, n)
+    for _ in range(2):
+        net.infer(Fn, P)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(5):
+        net.infer(Fn, P)
+    b.record()
+    torch.cuda.synchronize()
+    infer_ms = a.elapsed_time(b) / 5
+
+    def run(map_kind):
+        lat = lb.Lattice.from_workload(w, store="f32_dev") if map_kind != "all_high" else allh
+        if map_kind == "learned":
+            lat.set_mlp(net, every=every)
+        if map_kind != "all_high":
+            lat.step(steps)
+        m = lat.moments(mask=0b111)
+        du = np.sqrt((m["ux"] - ref["ux"]) ** 2 + (m["uy"] - ref["uy"]) ** 2)
+        e_u = float(du.max() / np.sqrt(ref["ux"] ** 2 + ref["uy"] ** 2).max())
+        phi = float((lat.effective_map() == 1).mean())
+        stats = lat.map_stats() if map_kind == "learned" else None
+        k = 2 * every
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        lat.step(k)
+        torch.cuda.synchronize()
+        mlups = n * k / (time.perf_counter() - t) / 1e6
+        out = {"e_u_vs_all_high": e_u, "phi_H": phi, "MLUPS": mlups, "variant": lat.info()["variant"]}
+        if stats:
+            out["map_updates"] = stats["updates"]
+            out["fallbacks"] = stats["fallbacks"]
+            t = time.perf_counter()
+            lat.learned_map_now()
+            torch.cuda.synchronize()
+            out["map_update_ms"] = (time.perf_counter() - t) * 1e3
+        return out
+
+    res = {m: run(m) for m in ("fixed", "learned", "all_high")}
+    return {"workload": f"long channel {nx}x{ny}, CFL 0.38, {steps} steps", "samples": samples,
+            "label": f"e3 > {threshold:g} on the all-D2Q36 run", "label_share": label_share,
+            "train": {"epochs": epochs, "seconds": train_s, "loss0": loss0, "loss": loss, "accuracy": acc},
+            "infer_ms_whole_lattice": infer_ms, "update_every": every, "maps": res}
+
+
 def run_reference(args, rank):
     """The oracle as the reference arm: each step advances a 512-column long channel of
     the headline's height, density ratio, Kn and map rule (a bounded sample of the
@@ -442,6 +525,7 @@ def main():
             forms[name]["e_u_steady_poiseuille_6000_steps"] = e
         forms["accuracy_cases"] = (f"the headline lattice after {PARITY_STEPS} steps against the FP64 oracle; "
                                    "steady Poiseuille 4x64, Kn 0.1, 6000 steps; max relative errors")
+        forms["learned_placement"] = config5_study(lb, torch)
 
     # secondary: three force-driven 1024 x 512 channels (Kn 0.02 / 0.1 / 0.5), one stream
     # each, stepped together

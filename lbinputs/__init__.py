@@ -196,6 +196,34 @@ def placement_channel(kn: float, region_map=None, nx=8, ny=64, u_lat=0.05, cfl=0
     return w
 
 
+def mlp_init(seed: int = 1007, nf: int = 8, nh: int = 64) -> np.ndarray:
+    """Seeded starting weights of the learned-placement network (8 -> 64 -> 64 -> 1),
+    packed W1 [nh][nf], b1, W2 [nh][nh], b2, W3 [nh], b3: normal with standard deviation
+    sqrt(2 / fan_in), zero biases."""
+    rng = np.random.default_rng(seed)
+    w1 = rng.standard_normal((nh, nf)) * math.sqrt(2.0 / nf)
+    w2 = rng.standard_normal((nh, nh)) * math.sqrt(2.0 / nh)
+    w3 = rng.standard_normal(nh) * math.sqrt(2.0 / nh)
+    return np.concatenate([w1.ravel(), np.zeros(nh), w2.ravel(), np.zeros(nh), w3, np.zeros(1)]).astype(np.float32)
+
+
+def wall_stratified_sample(ny: int, nx: int, n: int, seed: int = 1007) -> np.ndarray:
+    """n node indices (j * nx + i) of an ny x nx channel, the same number from every
+    distance to the nearer wall (each distance holds two rows), uniformly within it,
+    without replacement."""
+    rng = np.random.default_rng(seed)
+    dist = np.minimum(np.arange(ny), ny - 1 - np.arange(ny))
+    levels = np.unique(dist)
+    per = -(-n // len(levels))
+    out = []
+    for d in levels:
+        rows = np.nonzero(dist == d)[0]
+        pool = (rows[:, None] * nx + np.arange(nx)[None, :]).ravel()
+        out.append(rng.choice(pool, size=min(per, pool.size), replace=False))
+    idx = np.concatenate(out)
+    return np.sort(rng.choice(idx, size=min(n, idx.size), replace=False))
+
+
 def steady_steps(kn: float, dt: float) -> int:
     """Steps to two viscous times H^2 / nu (nu ~ Kn) of the placement channel."""
     return int(min(60000, max(4000, 2.0 / (kn * dt))))
