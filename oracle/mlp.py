@@ -68,6 +68,21 @@ def forward(theta, x):
     return sigmoid(z), (x, a1, h1, a2, h2, z)
 
 
+def forward_bf16_operands(theta, x):
+    """The forward pass with the precision of a tensor-core inference: BF16-rounded
+    weights and biases, and the inputs of the first two layers (the normalised features
+    and the first hidden activations) rounded to BF16 before each product; sums, GELU and
+    the output layer in FP64. x [B][8] (normalised) -> p [B]."""
+    P = unpack(round_bf16(theta))
+    xr = round_bf16(x)
+    a1 = xr @ P["W1"].T + P["b1"]
+    h1 = round_bf16(gelu(a1))
+    a2 = h1 @ P["W2"].T + P["b2"]
+    h2 = gelu(a2)
+    z = h2 @ P["W3"] + P["b3"][0]
+    return sigmoid(z)
+
+
 def loss(theta, x, y):
     p, _ = forward(theta, x)
     p = np.clip(p, 1e-300, 1.0 - 1e-16)

@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <random>
@@ -155,41 +156,134 @@ __global__ void to_bf16_kernel(const float *th, __nv_bfloat16 *wb)
     if (k < NPARAM) wb[k] = __float2bfloat16_rn(th[k]);
 }
 
-/* Inference: BF16 weights (held in shared memory as float), FP32 accumulation; one
- * thread per node; X [NF][n] raw features, out p [n]. */
-__global__ void infer_kernel(const __nv_bfloat16 *__restrict__ wb, const float *__restrict__ norm,
-                             const float *__restrict__ X, long long n, float *__restrict__ p)
+/* Inference on the tensor cores: mma.sync m16n8k16 with BF16 operands and FP32
+ * accumulation. A warp takes 16 nodes at a time. Layer 1 is the 16 x 16 (8 features,
+ * zero-padded) by 16 x 64 product; its GELU outputs are rounded to BF16 and, because
+ * the accumulator fragment of two neighbouring 8-column output tiles has exactly the
+ * element layout of one 16-wide operand fragment, feed layer 2 from registers; layer 2's
+ * GELU outputs meet W3 in FP32 (a dot product over the 64 hidden units, finished across
+ * the four lanes that share a row). The weight fragments are built in shared memory
+ * once per block. A node with a non-finite feature gets p = NaN. */
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
 {
-    __shared__ float s[NPARAM];
-    __shared__ float nm[2 * NF];
-    for (int k = threadIdx.x; k < NPARAM; k += blockDim.x) s[k] = __bfloat162float(wb[k]);
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16_raw(__nv_bfloat16 lo, __nv_bfloat16 hi)
+{
+    __nv_bfloat162 v;
+    v.x = lo;
+    v.y = hi;
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__global__ void __launch_bounds__(128) infer_mma_kernel(const __nv_bfloat16 *__restrict__ wb,
+                                                        const float *__restrict__ norm,
+                                                        const float *__restrict__ X, long long n,
+                                                        float *__restrict__ p)
+{
+    /* operand fragments of the weights: B[k][n] of layer 1 is W1[n][k] (k < 8, zero
+     * above), of layer 2 W2[n][k]; fragment register r of lane l holds the rows
+     * 2 (l % 4) + {0, 1} (+ 8 for r = 1) of column l / 4 */
+    __shared__ uint32_t w1f[8][32][2];
+    __shared__ uint32_t w2f[4][8][32][2];
+    __shared__ float b1s[NH], b2s[NH], w3s[NH], nm[2 * NF], b3s;
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+    for (int k = threadIdx.x; k < 8 * 32; k += blockDim.x) {
+        const int nt = k / 32, l = k % 32, col = 8 * nt + l / 4, row = 2 * (l % 4);
+        w1f[nt][l][0] = pack_bf16_raw(wb[OFF_W1 + col * NF + row], wb[OFF_W1 + col * NF + row + 1]);
+        w1f[nt][l][1] = pack_bf16_raw(zero, zero);
+    }
+    for (int k = threadIdx.x; k < 4 * 8 * 32; k += blockDim.x) {
+        const int kt = k / 256, nt = (k / 32) % 8, l = k % 32;
+        const int col = 8 * nt + l / 4, row = 16 * kt + 2 * (l % 4);
+        const __nv_bfloat16 *w = wb + OFF_W2 + col * NH;
+        w2f[kt][nt][l][0] = pack_bf16_raw(w[row], w[row + 1]);
+        w2f[kt][nt][l][1] = pack_bf16_raw(w[row + 8], w[row + 9]);
+    }
+    for (int k = threadIdx.x; k < NH; k += blockDim.x) {
+        b1s[k] = __bfloat162float(wb[OFF_B1 + k]);
+        b2s[k] = __bfloat162float(wb[OFF_B2 + k]);
+        w3s[k] = __bfloat162float(wb[OFF_W3 + k]);
+    }
     if (threadIdx.x < 2 * NF) nm[threadIdx.x] = norm[threadIdx.x];
+    if (threadIdx.x == 0) b3s = __bfloat162float(wb[OFF_B3]);
     __syncthreads();
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
-    float x[NF];
-    bool ok = true;
-    for (int f = 0; f < NF; ++f) {
-        x[f] = (X[(long long)f * n + c] - nm[f]) / nm[NF + f];
-        ok = ok && isfinite(x[f]);
+
+    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+    const long long tiles = (n + 15) / 16;
+    const long long stride = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < tiles; t += stride) {
+        const long long r0 = 16 * t + g, r1 = r0 + 8;   /* the two nodes (rows) of this lane */
+        /* layer-1 operand: normalised features 2q, 2q + 1 of both rows (columns 8..15 zero) */
+        float x[2][2];
+        bool ok0 = true, ok1 = true;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int f = 2 * q + e;
+            x[0][e] = r0 < n ? (X[(long long)f * n + r0] - nm[f]) / nm[NF + f] : 0.0f;
+            x[1][e] = r1 < n ? (X[(long long)f * n + r1] - nm[f]) / nm[NF + f] : 0.0f;
+            ok0 = ok0 && isfinite(x[0][e]);
+            ok1 = ok1 && isfinite(x[1][e]);
+        }
+        /* a node is usable when all eight features are finite: the four lanes of a row
+         * hold two each */
+        const unsigned m0 = __ballot_sync(0xffffffffu, !ok0), m1 = __ballot_sync(0xffffffffu, !ok1);
+        const unsigned qm = 0xfu << (4 * g);
+        ok0 = !(m0 & qm);
+        ok1 = !(m1 & qm);
+        if (!ok0) x[0][0] = x[0][1] = 0.0f;
+        if (!ok1) x[1][0] = x[1][1] = 0.0f;
+        const uint32_t a1[4] = {pack_bf16(x[0][0], x[0][1]), pack_bf16(x[1][0], x[1][1]), 0u, 0u};
+        /* layer 1 -> GELU -> BF16 operand fragments of layer 2 */
+        uint32_t a2[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            const uint32_t b[2] = {w1f[nt][lane][0], w1f[nt][lane][1]};
+            mma_bf16(c, a1, b);
+            const int col = 8 * nt + 2 * q;
+            const float h00 = gelu(c[0] + b1s[col]), h01 = gelu(c[1] + b1s[col + 1]);
+            const float h10 = gelu(c[2] + b1s[col]), h11 = gelu(c[3] + b1s[col + 1]);
+            const int kt = nt >> 1, hi = (nt & 1) * 2;
+            a2[kt][hi] = pack_bf16(h00, h01);
+            a2[kt][hi + 1] = pack_bf16(h10, h11);
+        }
+        /* layer 2 -> GELU -> W3 dot product */
+        float z0 = 0.0f, z1 = 0.0f;
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int kt = 0; kt < 4; ++kt) {
+                const uint32_t b[2] = {w2f[kt][nt][lane][0], w2f[kt][nt][lane][1]};
+                mma_bf16(c, a2[kt], b);
+            }
+            const int col = 8 * nt + 2 * q;
+            z0 = fmaf(gelu(c[0] + b2s[col]), w3s[col], z0);
+            z0 = fmaf(gelu(c[1] + b2s[col + 1]), w3s[col + 1], z0);
+            z1 = fmaf(gelu(c[2] + b2s[col]), w3s[col], z1);
+            z1 = fmaf(gelu(c[3] + b2s[col + 1]), w3s[col + 1], z1);
+        }
+        z0 += __shfl_xor_sync(0xffffffffu, z0, 1);
+        z0 += __shfl_xor_sync(0xffffffffu, z0, 2);
+        z1 += __shfl_xor_sync(0xffffffffu, z1, 1);
+        z1 += __shfl_xor_sync(0xffffffffu, z1, 2);
+        if (q == 0) {
+            if (r0 < n) p[r0] = ok0 ? 1.0f / (1.0f + expf(-(z0 + b3s))) : nanf("");
+            if (r1 < n) p[r1] = ok1 ? 1.0f / (1.0f + expf(-(z1 + b3s))) : nanf("");
+        }
     }
-    if (!ok) {
-        p[c] = nanf("");
-        return;
-    }
-    float hh[NH];
-    for (int i = 0; i < NH; ++i) {
-        float t = s[OFF_B1 + i];
-        for (int f = 0; f < NF; ++f) t = fmaf(s[OFF_W1 + i * NF + f], x[f], t);
-        hh[i] = gelu(t);
-    }
-    float z = s[OFF_B3];
-    for (int i = 0; i < NH; ++i) {
-        float t = s[OFF_B2 + i];
-        for (int k = 0; k < NH; ++k) t = fmaf(s[OFF_W2 + i * NH + k], hh[k], t);
-        z = fmaf(s[OFF_W3 + i], gelu(t), z);
-    }
-    p[c] = 1.0f / (1.0f + expf(-z));
 }
 
 }  // namespace lbm
@@ -283,8 +377,11 @@ namespace lbk {
 
 int mlp_infer_dev(lb_mlp *M, const float *x, int64_t n, float *p, void *stream)
 {
-    lbm::infer_kernel<<<(unsigned)((n + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(M->wb, M->norm, x,
-                                                                                                   (long long)n, p);
+    /* four warps per block, up to 8 blocks per SM resident (152 SMs): each warp walks
+     * its 16-node tiles with a grid stride */
+    const long long tiles = (n + 15) / 16;
+    const unsigned blocks = (unsigned)std::min<long long>((tiles + 3) / 4, 152LL * 8);
+    lbm::infer_mma_kernel<<<blocks, 128, 0, static_cast<cudaStream_t>(stream)>>>(M->wb, M->norm, x, (long long)n, p);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? LB_OK : mlp_err(LB_ERR_CUDA, std::string("lb_mlp_infer: ") + cudaGetErrorString(e));
 }

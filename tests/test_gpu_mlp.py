@@ -3,8 +3,8 @@
 
 The network's forward, backward, weight-gradient and Adam kernels train in FP32, so
 their results are compared with the FP64 oracle within FP32 accumulation error; the
-inference kernel uses BF16 weights and is compared with the oracle's forward pass on
-the BF16-rounded weights."""
+inference kernel runs on the tensor cores with BF16 weights and BF16 layer inputs, and is
+compared with the oracle's forward pass on the same BF16-rounded operands."""
 import numpy as np
 import pytest
 
@@ -85,7 +85,12 @@ def test_adam_steps_match_oracle():
     assert np.abs(d_got - d_ref).max() <= 2 * lr * 3 + 1e-6
 
 
-def test_bf16_inference_matches_oracle_on_rounded_weights():
+def test_bf16_inference_matches_oracle_on_rounded_operands():
+    """Tensor-core inference (BF16 weights and layer inputs, FP32 accumulation) against
+    the oracle's forward pass with the same operands rounded to BF16 and everything else
+    in FP64. A hidden activation whose FP32 and FP64 values straddle a BF16 rounding
+    boundary rounds the other way (one BF16 unit, 2^-8 relative) in a few of the 5000 x
+    64 of them: the bound is on the mean and, with room for those, on the maximum."""
     n = 5000
     x, y, nm = _data(n, 5)
     theta = omlp.init_params(9).astype(np.float32).astype(np.float64)
@@ -95,11 +100,28 @@ def test_bf16_inference_matches_oracle_on_rounded_weights():
     m.infer(_dev(x), out)
     p = out.cpu().numpy().astype(np.float64)
     xn = _norm(x, nm)
-    p_bf16, _ = omlp.forward(omlp.round_bf16(theta), xn)
+    p_ref = omlp.forward_bf16_operands(theta, xn)
     p_fp32, _ = omlp.forward(theta, xn)
-    assert np.abs(p - p_bf16).max() < 2e-5
-    # the rounding is really applied: full-precision weights give a visibly different p
+    d = np.abs(p - p_ref)
+    assert d.mean() < 2e-5 and d.max() < 2e-3, (d.mean(), d.max())
+    # the rounding is really applied: full-precision operands give a visibly different p
     assert np.abs(p - p_fp32).max() > 1e-4
+
+
+def test_inference_on_ragged_counts():
+    """Node counts that end inside a 16-node tile and inside a warp's share."""
+    import torch
+    theta = omlp.init_params(4).astype(np.float32).astype(np.float64)
+    _, _, nm = _data(5000, 11)   # normalisation from a large sample
+    m = _mlp(theta, nm)
+    for n in (1, 15, 17, 1000, 4099):
+        x, y, _ = _data(n, 12 + n)
+        out = torch.full((n + 5,), 7.0, device="cuda", dtype=torch.float32)
+        m.infer(_dev(x), out[:n])
+        got = out.cpu().numpy()
+        ref = omlp.forward_bf16_operands(theta, _norm(x, nm))
+        assert np.abs(got[:n] - ref).max() < 2e-3, n
+        assert np.all(got[n:] == 7.0), n   # nothing written past the end
 
 
 def test_inference_marks_nonfinite_inputs():
