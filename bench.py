@@ -36,7 +36,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from lbinputs import config2, config3, long_channel, poiseuille  # noqa: E402
+from lbinputs import config2, config3, long_channel, long_channel_density, poiseuille  # noqa: E402
 
 KN_SWEEP = (0.02, 0.1, 0.5)
 STORE_BYTES = {"f64": 8, "f32": 4, "f32_dev": 4, "f16_dev": 2, "bf16_dev": 2}
@@ -126,12 +126,18 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+STEP_SOURCES = ("lb_internal.h", "lb_common.cuh", "lb_store.cuh", "lb_step_impl.cuh", "lb_step.cu", "lb_pair.cuh")
+
+
 def kernel_sha():
+    """Hash of the sources of the step's kernels (the step kernels of every layout and the
+    pressure pass): DRAM counters taken on other sources are not reported."""
     import hashlib
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_1007_4895_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, f), "rb").read())
+        if f in STEP_SOURCES or f.startswith(("lb_step_st_", "lb_pair_")):
+            h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:12]
 
 
@@ -503,9 +509,16 @@ def main():
         specs = {"f32_dev": ("f32_dev", "nearest"), "f32": ("f32", "nearest"), "f16_dev": ("f16_dev", "nearest"),
                  "bf16_dev": ("bf16_dev", "nearest"), "f16_dev_sr": ("f16_dev", "stochastic"),
                  "bf16_dev_sr": ("bf16_dev", "stochastic")}
+        # the same deviation formats with the per-column reference density (lb_opts.rho0_col:
+        # the inlet-to-outlet density estimate), which takes the density offset out of the
+        # stored values
+        col = long_channel_density(w.nx, 2.0, 1.0)
+        specs_col = {"f32_dev_col": ("f32_dev", "nearest"), "f16_dev_sr_col": ("f16_dev", "stochastic"),
+                     "bf16_dev_sr_col": ("bf16_dev", "stochastic")}
         ref = None
-        for name, (store, rnd) in specs.items():
-            f = lb.Lattice.from_workload(w, store=store, rounding=rnd)
+        for name, (store, rnd) in list(specs.items()) + list(specs_col.items()):
+            kw = {"rho0_col": col} if name.endswith("_col") else {}
+            f = lb.Lattice.from_workload(w, store=store, rounding=rnd, **kw)
             if ref is None:
                 ref = oracle_reference_fields(PARITY_STEPS, f)
             f.step(PARITY_STEPS)
