@@ -123,7 +123,7 @@ typedef struct {
  * stream is a cudaStream_t. reduce_every > 0 runs the mass / residual reduction
  * every that many steps inside lb_step and flags divergence. variant < 0 lets
  * lb_create time the step-kernel layouts on this lattice and keep the fastest
- * (cached per process); 0 .. 8 forces one:
+ * (cached per process); 0 .. 9 forces one:
  *   0: one quad of nodes per thread, loads through L1;
  *   1: tiles streamed through shared memory by the tensor memory accelerator, two
  *      passes (FP32 / FP16 / BF16 storage only);
@@ -139,10 +139,13 @@ typedef struct {
  *   7: layout 0's threads, with the rows that need no boundary work computed in packed
  *      two-wide FP32 arithmetic on a folded form of the collision (FP32 and 16-bit
  *      storage);
- *   8: as 7, with the block order of 5 (only when the map has both sets).
+ *   8: as 7, with the block order of 5 (only when the map has both sets);
+ *   9: 7's arithmetic on every row, the neighbour rows brought into a per-thread ring
+ *      of shared-memory slots by asynchronous copies issued two nodes ahead, wall and
+ *      shadow-row updates done by the same kernel (FP32 and 16-bit storage).
  * A layout this lattice cannot use falls back to 0. All layouts give the same result
  * (0, 2, 3 and 4 the same bits; 1, 5, 6 the same bits as 0 or differing in rounding;
- * 7 and 8 differ from 0 in rounding). */
+ * 7, 8 and 9 differ from 0 in rounding). */
 typedef struct {
     int32_t store;
     int32_t iface;

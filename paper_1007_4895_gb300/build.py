@@ -18,11 +18,12 @@ LIB = os.path.join(HERE, "liblbgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lb_api.cu", "lb_step.cu", "lb_step_st_f64.cu", "lb_step_st_f32.cu", "lb_step_st_f32dev.cu",
            "lb_step_st_f16.cu", "lb_step_st_bf16.cu", "lb_pair_f32.cu", "lb_pair_f32dev.cu", "lb_pair_f16.cu",
-           "lb_pair_bf16.cu", "lb_step3.cu", "lb_stream.cu", "lb_aux.cu", "lb_mlp.cu", "lb_noalloc.cu",
+           "lb_pair_bf16.cu", "lb_ring_f32.cu", "lb_ring_f32dev.cu", "lb_ring_f16.cu", "lb_ring_bf16.cu", "lb_step3.cu", "lb_stream.cu", "lb_aux.cu", "lb_mlp.cu", "lb_noalloc.cu",
            "quadrature.cpp"]
 # The paired-arithmetic layout (lb_pair.cuh) is held to the oracle's tolerance, not to
 # the other layouts' bits, and is built with multiply-add contraction on.
-CONTRACT = {"lb_pair_f32.cu", "lb_pair_f32dev.cu", "lb_pair_f16.cu", "lb_pair_bf16.cu"}
+CONTRACT = {"lb_pair_f32.cu", "lb_pair_f32dev.cu", "lb_pair_f16.cu", "lb_pair_bf16.cu", "lb_ring_f32.cu",
+            "lb_ring_f32dev.cu", "lb_ring_f16.cu", "lb_ring_bf16.cu"}
 
 
 def nvcc() -> str:

@@ -562,7 +562,8 @@ int upload_tiles(lb_ctx *c)
  * (lb_step_impl.cuh); 4: streamed (lb_stream.cu); 5: variant 0 with the blocks that
  * hold high-order rows launched first; 6: as 5, with two nodes per thread in the bands
  * that hold high-order rows; 7: layout 0's threads with paired FP32 arithmetic on the
- * rows without boundary work (lb_pair.cuh); 8: 7 with the block order of 5. */
+ * rows without boundary work (lb_pair.cuh); 8: 7 with the block order of 5; 9: 7's
+ * arithmetic fed by a per-thread ring of asynchronous copies (lb_ring.cuh). */
 template <typename R>
 void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
 {
@@ -598,6 +599,10 @@ void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
             lbk::launch_pair(c->store, q, c->stream);
             return;
         }
+        if (variant == 9) {
+            lbk::launch_ring(c->store, p, c->stream);
+            return;
+        }
     }
     if (variant == 6 && c->bdesc_narrow) {
         StepParams<R> q = p;
@@ -617,12 +622,12 @@ void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
 /* layouts this context can run */
 bool variant_available(const lb_ctx *c, int v)
 {
-    if (c->d_dcol && v != 0 && v != 5 && v != 7 && v != 8) return false;   /* per-column reference density */
-    if (v == 7 || v == 8) {
+    if (c->d_dcol && v != 0 && v != 5 && v != 7 && v != 8 && v != 9) return false;   /* per-column reference density */
+    if (v == 7 || v == 8 || v == 9) {
         /* paired FP32 arithmetic: FP32 and 16-bit storage, 32-bit element offsets */
         const size_t span = std::max(c->q[0], c->q[1]) * (size_t)(c->ny + 2 * LB_GHOST_ROWS) * c->pitch;
         if (use_f64(c) || !c->d_ctab || span >= (1ull << 32)) return false;
-        return v == 7 || c->border_used;
+        return v != 8 || c->border_used;
     }
     if (v == 1) return c->tma_ok;
     if (v == 2 || v == 3) return c->edge_stream != nullptr;

@@ -134,11 +134,14 @@ void launch_aux(int store, const StepParams<R> &p, const int2 *list, int n, void
  * with its blocks launched in block_order, 6 the same kernel on block_desc (two nodes
  * per thread in high-order bands), 7 layout 0's threads with paired FP32 arithmetic on
  * the rows without boundary work (lb_pair.cuh; FP32 and 16-bit storage), 8 layout 7
- * with its blocks launched in block_order */
-#define LB_NUM_VARIANTS 9
+ * with its blocks launched in block_order, 9 layout 7's arithmetic fed by a per-thread
+ * ring of asynchronous copies, boundary work in the same kernel (lb_ring.cuh) */
+#define LB_NUM_VARIANTS 10
 /* layout 7 / 8: p.block_order selects between them (FP32 and 16-bit storage); p.ctab
  * must hold the tables that launch_pair_table wrote for this lattice */
 void launch_pair(int store, const StepParams<float> &p, void *stream);
+/* layout 9 (FP32 and 16-bit storage; p.ctab as for launch_pair) */
+void launch_ring(int store, const StepParams<float> &p, void *stream);
 size_t pair_table_bytes();
 void launch_pair_table(const StepParams<float> &p, void *dst, void *stream);
 

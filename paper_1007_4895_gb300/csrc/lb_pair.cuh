@@ -142,6 +142,128 @@ struct PairStencil {
     T v[4], y[3][4], l[2], r[2];
 };
 
+/* The per-node coefficients of the folded collision for a quad (two pairs), from its
+ * sums rd = sum w d, jx = sum w xi_x d, jy = sum w xi_y d. */
+struct PairNode {
+    float2 ux[2], uy[2], P[2], B[2], nom[2], dr[2];
+};
+
+template <bool FORCE>
+__device__ __forceinline__ PairNode pair_node_state(const StepParams<float> &p, const float2 (&rd)[2],
+                                                    const float2 (&jx)[2], const float2 (&jy)[2])
+{
+    PairNode nd;
+    const float rho0 = p.rho0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float uxe[2], uye[2], pe[2], be[2], oe[2], de[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float rdv = e ? rd[h].y : rd[h].x;
+            const float rho = rho0 + rdv;
+            const float inv = 1.0f / rho;
+            const float u = (e ? jx[h].y : jx[h].x) * inv, v = (e ? jy[h].y : jy[h].x) * inv;
+            const float o = p.dt / tau_of(p, inv);
+            float b = o * fmaf(-0.5f * rho, usq_of(u, v), rdv);
+            de[e] = p.dt * rho;
+            if constexpr (FORCE) b = fmaf(-de[e], xi_dot(p.gx, p.gy, u, v), b);
+            uxe[e] = u;
+            uye[e] = v;
+            pe[e] = o * rho;
+            be[e] = b;
+            oe[e] = -o;
+        }
+        nd.ux[h] = make_float2(uxe[0], uxe[1]);
+        nd.uy[h] = make_float2(uye[0], uye[1]);
+        nd.P[h] = make_float2(pe[0], pe[1]);
+        nd.B[h] = make_float2(be[0], be[1]);
+        nd.nom[h] = make_float2(oe[0], oe[1]);
+        nd.dr[h] = make_float2(de[0], de[1]);
+    }
+    return nd;
+}
+
+/* The increment of one population at a quad (collision and force, x flux, y flux), from
+ * its deviations v (two pairs); xh(i) gives the x halos, i = 0, 1 at columns x0-2, x0-1
+ * and i = 2, 3 at x0+4, x0+5 (asked for when c_x != 0), yw(h, i) the pair h of the y
+ * window rows i = 0, 1, 2 at rows j-2s, j-s, j+s with s = sign(xi_y) (asked for when
+ * c_y != 0), both decoded to deviations. */
+template <bool FORCE, typename XH, typename YW>
+__device__ __forceinline__ void pair_increment(const PairC &pc, const PairC2 &pc2, const PairNode &nd,
+                                               const float2 (&v)[2], const XH &xh, const YW &yw, float2 (&c)[2])
+{
+    /* collision and force */
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float2 eu = fma2(pc.cy2, nd.uy[h], mul2(pc.cx2, nd.ux[h]));
+        const float2 t = fma2(mul2(f2(0.5f), eu), eu, eu);
+        c[h] = fma2(nd.nom[h], v[h], fma2(nd.P[h], t, nd.B[h]));
+        if constexpr (FORCE) c[h] = fma2(nd.dr[h], fma2(pc2.gxi2, eu, pc2.gxi2), c[h]);
+    }
+    /* x flux (Sec. 3.1, mirrored for negative velocities) */
+    if (pc.crx != 0.0f) {
+        const float vv[4] = {v[0].x, v[0].y, v[1].x, v[1].y};
+        const float l0 = xh(0), l1 = xh(1), r0 = xh(2), r1 = xh(3);
+        float Dx[4];
+        if (pc.crx > 0.0f) {
+            float d[6], n[6], m[5];
+            d[0] = l1 - l0;
+            d[1] = vv[0] - l1;
+            d[2] = vv[1] - vv[0];
+            d[3] = vv[2] - vv[1];
+            d[4] = vv[3] - vv[2];
+            d[5] = r0 - vv[3];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) n[i] = neg_part(d[i]);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) m[i] = minmod_n(d[i], d[i + 1], n[i], n[i + 1]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Dx[k] = fmaf(pc.kx, m[k + 1] - m[k], d[k + 1]);
+        } else {
+            float e[6], n[6], m[5];
+            e[0] = vv[0] - l1;
+            e[1] = vv[1] - vv[0];
+            e[2] = vv[2] - vv[1];
+            e[3] = vv[3] - vv[2];
+            e[4] = r0 - vv[3];
+            e[5] = r1 - r0;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) n[i] = neg_part(e[i]);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) m[i] = minmod_n(e[i], e[i + 1], n[i], n[i + 1]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Dx[k] = fmaf(-pc.kx, m[k + 1] - m[k], e[k + 1]);
+        }
+        c[0] = fma2(pc.ncx2, make_float2(Dx[0], Dx[1]), c[0]);
+        c[1] = fma2(pc.ncx2, make_float2(Dx[2], Dx[3]), c[1]);
+    }
+    /* y flux on the window W = (f_{j-2s}, f_{j-s}, f_j, f_{j+s}), s = sign(xi_y): the
+     * printed flux for xi_y > 0 and its mirror image for xi_y < 0 are both
+     *   c_y (F^{j+1/2} - F^{j-1/2}) = |c_y| (d1 + k (minmod(d1, d2) - minmod(d0, d1)))
+     * with d0, d1, d2 the differences along W (the mirror image reverses W and flips the
+     * sign of every difference, and minmod is odd) */
+    if (pc.ystep != 0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float2 w0 = yw(h, 0), w1 = yw(h, 1), w3 = yw(h, 2);
+            const float2 d0 = sub2(w1, w0), d1 = sub2(v[h], w1), d2 = sub2(w3, v[h]);
+            float2 ma, mb;
+            {
+                const float lo = fminf(d1.x, 0.0f), hi = fmaxf(d1.x, 0.0f);
+                ma.x = fminf(fmaxf(d0.x, lo), hi);
+                mb.x = fminf(fmaxf(d2.x, lo), hi);
+            }
+            {
+                const float lo = fminf(d1.y, 0.0f), hi = fmaxf(d1.y, 0.0f);
+                ma.y = fminf(fmaxf(d0.y, lo), hi);
+                mb.y = fminf(fmaxf(d2.y, lo), hi);
+            }
+            const float2 Dy = fma2(pc.ky2, sub2(mb, ma), d1);
+            c[h] = fma2(pc.nacy2, Dy, c[h]);
+        }
+    }
+}
+
 /* One quad of a row without boundary work. */
 template <int ST, int Q, bool COL, bool FORCE>
 __device__ __forceinline__ void pair_cells(const StepParams<float> &p, int s, int x0, int j, const PairC *pcs,
@@ -188,33 +310,7 @@ __device__ __forceinline__ void pair_cells(const StepParams<float> &p, int s, in
         }
     }
     /* 2. per-node collision coefficients (and the force weight) */
-    float2 ux[2], uy[2], P[2], B[2], nom[2], dr[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        float uxe[2], uye[2], pe[2], be[2], oe[2], de[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const float rdv = e ? rd[h].y : rd[h].x;
-            const float rho = rho0 + rdv;
-            const float inv = 1.0f / rho;
-            const float u = (e ? jx[h].y : jx[h].x) * inv, v = (e ? jy[h].y : jy[h].x) * inv;
-            const float o = p.dt / tau_of(p, inv);
-            float b = o * fmaf(-0.5f * rho, usq_of(u, v), rdv);
-            de[e] = p.dt * rho;
-            if constexpr (FORCE) b = fmaf(-de[e], xi_dot(p.gx, p.gy, u, v), b);
-            uxe[e] = u;
-            uye[e] = v;
-            pe[e] = o * rho;
-            be[e] = b;
-            oe[e] = -o;
-        }
-        ux[h] = make_float2(uxe[0], uxe[1]);
-        uy[h] = make_float2(uye[0], uye[1]);
-        P[h] = make_float2(pe[0], pe[1]);
-        B[h] = make_float2(be[0], be[1]);
-        nom[h] = make_float2(oe[0], oe[1]);
-        dr[h] = make_float2(de[0], de[1]);
-    }
+    const PairNode nd = pair_node_state<FORCE>(p, rd, jx, jy);
 
     /* stores: plain 16-byte vectors, or per node for pressure columns, a ragged edge and
      * periodic ghost columns (the row has no ghost-row images here) */
@@ -249,79 +345,11 @@ __device__ __forceinline__ void pair_cells(const StepParams<float> &p, int s, in
         float2 v[2], c[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) v[h] = dec2(pair_of(S.v, h), pc2.winv2, 2 * h);
-        /* collision and force */
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const float2 eu = fma2(pc.cy2, uy[h], mul2(pc.cx2, ux[h]));
-            const float2 t = fma2(mul2(f2(0.5f), eu), eu, eu);
-            c[h] = fma2(nom[h], v[h], fma2(P[h], t, B[h]));
-            if constexpr (FORCE) c[h] = fma2(dr[h], fma2(pc2.gxi2, eu, pc2.gxi2), c[h]);
-        }
-        /* x flux (Sec. 3.1, mirrored for negative velocities) */
-        if (pc.crx != 0.0f) {
-            const float l0 = dec1(S.l[0], pc2.winv2.x, 0), l1 = dec1(S.l[1], pc2.winv2.x, 1);
-            const float r0 = dec1(S.r[0], pc2.winv2.x, 6), r1 = dec1(S.r[1], pc2.winv2.x, 7);
-            const float vv[4] = {v[0].x, v[0].y, v[1].x, v[1].y};
-            float Dx[4];
-            if (pc.crx > 0.0f) {
-                float d[6], n[6], m[5];
-                d[0] = l1 - l0;
-                d[1] = vv[0] - l1;
-                d[2] = vv[1] - vv[0];
-                d[3] = vv[2] - vv[1];
-                d[4] = vv[3] - vv[2];
-                d[5] = r0 - vv[3];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) n[i] = neg_part(d[i]);
-#pragma unroll
-                for (int i = 0; i < 5; ++i) m[i] = minmod_n(d[i], d[i + 1], n[i], n[i + 1]);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) Dx[k] = fmaf(pc.kx, m[k + 1] - m[k], d[k + 1]);
-            } else {
-                float e[6], n[6], m[5];
-                e[0] = vv[0] - l1;
-                e[1] = vv[1] - vv[0];
-                e[2] = vv[2] - vv[1];
-                e[3] = vv[3] - vv[2];
-                e[4] = r0 - vv[3];
-                e[5] = r1 - r0;
-#pragma unroll
-                for (int i = 0; i < 6; ++i) n[i] = neg_part(e[i]);
-#pragma unroll
-                for (int i = 0; i < 5; ++i) m[i] = minmod_n(e[i], e[i + 1], n[i], n[i + 1]);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) Dx[k] = fmaf(-pc.kx, m[k + 1] - m[k], e[k + 1]);
-            }
-            c[0] = fma2(pc.ncx2, make_float2(Dx[0], Dx[1]), c[0]);
-            c[1] = fma2(pc.ncx2, make_float2(Dx[2], Dx[3]), c[1]);
-        }
-        /* y flux on the window W = (f_{j-2s}, f_{j-s}, f_j, f_{j+s}), s = sign(xi_y): the
-         * printed flux for xi_y > 0 and its mirror image for xi_y < 0 are both
-         *   c_y (F^{j+1/2} - F^{j-1/2}) = |c_y| (d1 + k (minmod(d1, d2) - minmod(d0, d1)))
-         * with d0, d1, d2 the differences along W (the mirror image reverses W and flips
-         * the sign of every difference, and minmod is odd) */
-        if (pc.ystep != 0) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const float2 w0 = dec2(pair_of(S.y[0], h), pc2.winv2, 2 * h);
-                const float2 w1 = dec2(pair_of(S.y[1], h), pc2.winv2, 2 * h);
-                const float2 w3 = dec2(pair_of(S.y[2], h), pc2.winv2, 2 * h);
-                const float2 d0 = sub2(w1, w0), d1 = sub2(v[h], w1), d2 = sub2(w3, v[h]);
-                float2 ma, mb;
-                {
-                    const float lo = fminf(d1.x, 0.0f), hi = fmaxf(d1.x, 0.0f);
-                    ma.x = fminf(fmaxf(d0.x, lo), hi);
-                    mb.x = fminf(fmaxf(d2.x, lo), hi);
-                }
-                {
-                    const float lo = fminf(d1.y, 0.0f), hi = fmaxf(d1.y, 0.0f);
-                    ma.y = fminf(fmaxf(d0.y, lo), hi);
-                    mb.y = fminf(fmaxf(d2.y, lo), hi);
-                }
-                const float2 Dy = fma2(pc.ky2, sub2(mb, ma), d1);
-                c[h] = fma2(pc.nacy2, Dy, c[h]);
-            }
-        }
+        auto xh = [&](int i) -> float {
+            return i < 2 ? dec1(S.l[i], pc2.winv2.x, i) : dec1(S.r[i - 2], pc2.winv2.x, i + 4);
+        };
+        auto yw = [&](int h, int i) -> float2 { return dec2(pair_of(S.y[i], h), pc2.winv2, 2 * h); };
+        pair_increment<FORCE>(pc, pc2, nd, v, xh, yw, c);
         /* store */
         float2 dn[2];
 #pragma unroll

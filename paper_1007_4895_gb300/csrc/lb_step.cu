@@ -20,6 +20,8 @@ void launch_step_split_store(const StepParams<typename Store<ST>::R> &p, int rb,
                              void *stream, void *edge_stream);
 template <int ST>
 void launch_pair_store(const StepParams<float> &p, void *stream);
+template <int ST>
+void launch_ring_store(const StepParams<float> &p, void *stream);
 
 /* ---------------------------------------------------------------- mode A -- */
 
@@ -332,6 +334,17 @@ template <typename R>
 void launch_step(int store, const StepParams<R> &p, void *stream)
 {
     LB_DISPATCH(store, if constexpr (store_matches<R, ST>()) launch_step_store<ST>(p, stream));
+}
+
+void launch_ring(int store, const StepParams<float> &p, void *stream)
+{
+    switch (store) {
+        case 1: launch_ring_store<1>(p, stream); break;
+        case 2: launch_ring_store<2>(p, stream); break;
+        case 3: launch_ring_store<3>(p, stream); break;
+        case 4: launch_ring_store<4>(p, stream); break;
+        default: break;
+    }
 }
 
 void launch_pair(int store, const StepParams<float> &p, void *stream)

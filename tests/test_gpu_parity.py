@@ -132,7 +132,7 @@ def test_oscillating_wall_fp64():
     assert max(errs.values()) < F64_TOL, errs
 
 
-LAYOUTS = [0, 1, 2, 3, 4, 5, 6, 7, 8]
+LAYOUTS = [0, 1, 2, 3, 4, 5, 6, 7, 8, 9]
 
 
 @pytest.mark.parametrize("variant", LAYOUTS)
@@ -142,7 +142,7 @@ def test_every_kernel_layout_matches_oracle(variant):
     reproduce the oracle."""
     w = ragged_workload()
     for store, tol in (("f64", F64_TOL), ("f32_dev", 1e-6), ("f32", 1e-4)):
-        if store == "f64" and variant in (1, 4, 7, 8):   # FP32 / 16-bit storage only
+        if store == "f64" and variant in (1, 4, 7, 8, 9):   # FP32 / 16-bit storage only
             continue
         lat, o, eff, got, ref = run_both(w, store, 60, variant=variant)
         assert lat.info()["variant"] == variant
@@ -214,7 +214,7 @@ def _col_pair(w, store, rho0_col, **kw):
     return a, b, o
 
 
-@pytest.mark.parametrize("variant", [0, 7])
+@pytest.mark.parametrize("variant", [0, 7, 9])
 @pytest.mark.parametrize("store", ["f32_dev", "f16_dev", "bf16_dev"])
 @pytest.mark.parametrize("case", ["ragged", "pressure_channel"])
 def test_constant_per_column_reference_changes_nothing(store, case, variant):
@@ -407,11 +407,11 @@ def test_register_block_layouts_equal_quad_layout(store, variant):
         assert np.array_equal(a.populations(s), b.populations(s)), (store, variant, s)
 
 
-@pytest.mark.parametrize("variant", [7, 8])
+@pytest.mark.parametrize("variant", [7, 8, 9])
 @pytest.mark.parametrize("store", ["f32_dev", "f32", "f16_dev", "bf16_dev_sr", "f16_dev_sr"])
 @pytest.mark.parametrize("case", ["ragged", "pressure_channel", "bands_paper", "periodic_box"])
 def test_paired_layout_agrees_with_quad_layout(store, case, variant):
-    """Layouts 7 and 8 fold the collision into per-node coefficients, compute node pairs
+    """Layouts 7, 8 and 9 fold the collision into per-node coefficients, compute node pairs
     with packed FP32 instructions and are built with multiply-add contraction, so they
     round differently from layout 0; the update is the same (stencil, walls, shadows,
     ghost copies, pressure columns, random bits). After 40 steps the two agree to
