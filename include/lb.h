@@ -123,7 +123,7 @@ typedef struct {
  * stream is a cudaStream_t. reduce_every > 0 runs the mass / residual reduction
  * every that many steps inside lb_step and flags divergence. variant < 0 lets
  * lb_create time the step-kernel layouts on this lattice and keep the fastest
- * (cached per process); 0 .. 9 forces one:
+ * (cached per process); 0 .. 10 forces one:
  *   0: one quad of nodes per thread, loads through L1;
  *   1: tiles streamed through shared memory by the tensor memory accelerator, two
  *      passes (FP32 / FP16 / BF16 storage only);
@@ -142,10 +142,13 @@ typedef struct {
  *   8: as 7, with the block order of 5 (only when the map has both sets);
  *   9: 7's arithmetic on every row, the neighbour rows brought into a per-thread ring
  *      of shared-memory slots by asynchronous copies issued two nodes ahead, wall and
- *      shadow-row updates done by the same kernel (FP32 and 16-bit storage).
+ *      shadow-row updates done by the same kernel (FP32 and 16-bit storage);
+ *  10: 9's arithmetic in one persistent launch: warps take rows of 128 columns from
+ *      per-SM queues (longest rows first), with the population loop unrolled over the
+ *      velocity set (D2Q9 with D2Q16 or D2Q36; FP32 and 16-bit storage).
  * A layout this lattice cannot use falls back to 0. All layouts give the same result
  * (0, 2, 3 and 4 the same bits; 1, 5, 6 the same bits as 0 or differing in rounding;
- * 7, 8 and 9 differ from 0 in rounding). */
+ * 7, 8 and 9 differ from 0 in rounding; 10 the same bits as 9). */
 typedef struct {
     int32_t store;
     int32_t iface;

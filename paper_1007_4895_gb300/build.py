@@ -18,12 +18,15 @@ LIB = os.path.join(HERE, "liblbgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lb_api.cu", "lb_step.cu", "lb_step_st_f64.cu", "lb_step_st_f32.cu", "lb_step_st_f32dev.cu",
            "lb_step_st_f16.cu", "lb_step_st_bf16.cu", "lb_pair_f32.cu", "lb_pair_f32dev.cu", "lb_pair_f16.cu",
-           "lb_pair_bf16.cu", "lb_ring_f32.cu", "lb_ring_f32dev.cu", "lb_ring_f16.cu", "lb_ring_bf16.cu", "lb_step3.cu", "lb_stream.cu", "lb_aux.cu", "lb_mlp.cu", "lb_noalloc.cu",
+           "lb_pair_bf16.cu", "lb_ring_f32.cu", "lb_ring_f32dev.cu", "lb_ring_f16.cu", "lb_ring_bf16.cu",
+           "lb_ring2_f32_q16.cu", "lb_ring2_f32_q36.cu", "lb_ring2_f32dev_q16.cu", "lb_ring2_f32dev_q36.cu", "lb_ring2_f16_q16.cu", "lb_ring2_f16_q36.cu", "lb_ring2_bf16_q16.cu", "lb_ring2_bf16_q36.cu",
+           "lb_step3.cu", "lb_stream.cu", "lb_aux.cu", "lb_mlp.cu", "lb_noalloc.cu",
            "quadrature.cpp"]
 # The paired-arithmetic layout (lb_pair.cuh) is held to the oracle's tolerance, not to
 # the other layouts' bits, and is built with multiply-add contraction on.
 CONTRACT = {"lb_pair_f32.cu", "lb_pair_f32dev.cu", "lb_pair_f16.cu", "lb_pair_bf16.cu", "lb_ring_f32.cu",
-            "lb_ring_f32dev.cu", "lb_ring_f16.cu", "lb_ring_bf16.cu"}
+            "lb_ring_f32dev.cu", "lb_ring_f16.cu", "lb_ring_bf16.cu"} | {
+                f"lb_ring2_{f}_q{q}.cu" for f in ("f32", "f32dev", "f16", "bf16") for q in (16, 36)}
 
 
 def nvcc() -> str:

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <tuple>
@@ -116,6 +117,16 @@ struct lb_ctx {
     bool bdesc_narrow = false;      /* some band runs two nodes per thread */
     void *d_dcol = nullptr;         /* per-column reference density: delta per storage column (R) */
     void *d_ctab = nullptr;         /* layouts 7 / 8: per-population constant tables */
+    int nsm = 0;                    /* SMs of the device */
+    /* layout 10: row queues (per SM and shared), their counters, and the constants
+     * passed in kernel-parameter space */
+    std::vector<uint32_t> rrows_h;
+    std::vector<int2> rdesc_h;
+    uint32_t *d_rrows = nullptr;
+    size_t rrows_cap = 0;
+    int2 *d_rdesc = nullptr;
+    uint32_t *d_rctr = nullptr;
+    std::unique_ptr<lbk::RingTab> rtab;
     uint32_t dcol_hash = 0;         /* FNV-1a of those deltas (0: one reference density) */
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     /* learned placement */
@@ -468,6 +479,92 @@ int build_edge_lists(lb_ctx *c)
                                                   c->stream), "block order upload"))
             return e;
     }
+    /* layout 10 row queues. Rows are grouped in block units of LB_STEP_BY rows of a tile,
+     * the units sorted most work first (raster order among equals) and dealt round-robin
+     * to one queue per SM, the last tenth to the shared queue; within a queue the rows
+     * are then sorted by their own work, longest first (stable: the rows of a unit stay
+     * together among equals). Row kinds (the kernel's RING_*): lean (no boundary work;
+     * pressure columns count as none), row (diffuse wall, ghost-row copies, shadow or
+     * periodic ghost columns), edge (a tile ending inside the last 128 columns, no
+     * boundary work), general (stochastic rounding, or boundary work in such a tile);
+     * mode-A interface rows are left out. Work of a row, in units of a population of
+     * a lean row: its set size, times 1.25 with a wall, ghost rows or ghost columns, plus
+     * twice the other set's size for a shadow; edge rows count 1.5, general rows 2. */
+    c->rrows_h.clear();
+    c->rdesc_h.clear();
+    if (c->nsm > 0 && c->ny <= 0xffff && c->ntx <= 0x3fff) {
+        const bool sr = c->opts.rounding == LB_ROUND_STOCHASTIC &&
+                        (c->store == LB_STORE_F16_DEV || c->store == LB_STORE_BF16_DEV);
+        const int nby = (c->ny + LB_STEP_BY - 1) / LB_STEP_BY;
+        struct Row {
+            int cost;
+            uint32_t item;
+        };
+        struct Unit {
+            int cost;
+            Row rows[LB_STEP_BY];
+            int n;
+        };
+        std::vector<Unit> K;
+        for (int by = 0; by < nby; ++by)
+            for (int tx = 0; tx < c->ntx; ++tx) {
+                Unit u{0, {}, 0};
+                const bool ragged = (tx + 1) * LB_TILE_X > c->nx;
+                const bool gcols = px && (tx == 0 || (tx + 1) * LB_TILE_X > c->nx - LB_GHOST);
+                for (int j = by * LB_STEP_BY; j < std::min(c->ny, (by + 1) * LB_STEP_BY); ++j) {
+                    const uint8_t f = c->tmap[(size_t)j * c->ntx + tx];
+                    if (f & LB_TILE_IFACE) continue;
+                    const int q = c->q[f & LB_TILE_HIGH], qt = c->q[(f & LB_TILE_HIGH) ^ 1];
+                    const bool images = py ? (j < 2 || j >= c->ny - 2) : (j == 0 || j == c->ny - 1);
+                    const bool shadow = f & LB_TILE_SHADOW;
+                    const bool boundary = images || shadow || gcols;
+                    const uint32_t kind = sr ? 3u : ragged ? (boundary ? 3u : 1u) : boundary ? 2u : 0u;
+                    int cost = 4 * q;
+                    if (kind == 2u) cost = 5 * q + (shadow ? 8 * qt : 0);
+                    if (kind == 1u) cost = 6 * q;
+                    if (kind == 3u) cost = 8 * q;
+                    u.cost += cost;
+                    u.rows[u.n++] = Row{cost, ((uint32_t)j << 16) | (kind << 14) | (uint32_t)tx};
+                }
+                if (u.n > 0) K.push_back(u);
+            }
+        std::stable_sort(K.begin(), K.end(), [](const Unit &a, const Unit &b) { return a.cost > b.cost; });
+        const int nq = c->nsm;
+        const size_t shared_from = K.size() - K.size() / 10;
+        std::vector<std::vector<Row>> Qs(nq + 1);
+        for (size_t i = 0; i < K.size(); ++i) {
+            std::vector<Row> &dst = i < shared_from ? Qs[i % nq] : Qs[nq];
+            dst.insert(dst.end(), K[i].rows, K[i].rows + K[i].n);
+        }
+        for (auto &q : Qs) {
+            std::stable_sort(q.begin(), q.end(), [](const Row &a, const Row &b) { return a.cost > b.cost; });
+            c->rdesc_h.push_back(make_int2((int)c->rrows_h.size(), (int)q.size()));
+            for (const Row &r : q) c->rrows_h.push_back(r.item);
+        }
+    }
+    if (!c->rrows_h.empty()) {
+        if (!c->d_rctr) {   /* counters: zero between launches */
+            c->d_rctr = static_cast<uint32_t *>(own(c, sizeof(uint32_t) * (c->nsm + 2)));
+            c->d_rdesc = static_cast<int2 *>(own(c, sizeof(int2) * (c->nsm + 1)));
+            if (!c->d_rctr || !c->d_rdesc) return fail(LB_ERR_NOMEM, "device allocation failed");
+            if (int e = cuda_check(c, cudaMemsetAsync(c->d_rctr, 0, sizeof(uint32_t) * (c->nsm + 2), c->stream),
+                                   "row queue counters"))
+                return e;
+        }
+        if (c->rrows_h.size() > c->rrows_cap) {
+            const size_t cap = std::max(c->rrows_h.size(), 2 * c->rrows_cap);
+            uint32_t *d = static_cast<uint32_t *>(own(c, cap * sizeof(uint32_t)));
+            if (!d) return fail(LB_ERR_NOMEM, "device allocation failed");
+            c->d_rrows = d;
+            c->rrows_cap = cap;
+        }
+        if (int e = cuda_check(c, cudaMemcpyAsync(c->d_rrows, c->rrows_h.data(), c->rrows_h.size() * sizeof(uint32_t),
+                                                  cudaMemcpyHostToDevice, c->stream), "row queue upload"))
+            return e;
+        if (int e = cuda_check(c, cudaMemcpyAsync(c->d_rdesc, c->rdesc_h.data(), c->rdesc_h.size() * sizeof(int2),
+                                                  cudaMemcpyHostToDevice, c->stream), "row queue upload"))
+            return e;
+    }
     /* compact-state segments */
     compact_segments(c, c->tmap, c->seg_h, c->nseg);
     if (!c->seg_h.empty()) {
@@ -603,6 +700,11 @@ void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
             lbk::launch_ring(c->store, p, c->stream);
             return;
         }
+        if (variant == 10) {
+            const lbk::RowQueues rq{c->d_rrows, c->d_rdesc, c->d_rctr, c->nsm};
+            lbk::launch_ring_units(c->store, p, *c->rtab, rq, (int)((c->rrows_h.size() + 7) / 8), c->stream);
+            return;
+        }
     }
     if (variant == 6 && c->bdesc_narrow) {
         StepParams<R> q = p;
@@ -622,11 +724,13 @@ void launch_variant(lb_ctx *c, int variant, const StepParams<R> &p)
 /* layouts this context can run */
 bool variant_available(const lb_ctx *c, int v)
 {
-    if (c->d_dcol && v != 0 && v != 5 && v != 7 && v != 8 && v != 9) return false;   /* per-column reference density */
-    if (v == 7 || v == 8 || v == 9) {
+    if (c->d_dcol && v != 0 && v != 5 && v != 7 && v != 8 && v != 9 && v != 10) return false;   /* per-column reference density */
+    if (v == 7 || v == 8 || v == 9 || v == 10) {
         /* paired FP32 arithmetic: FP32 and 16-bit storage, 32-bit element offsets */
         const size_t span = std::max(c->q[0], c->q[1]) * (size_t)(c->ny + 2 * LB_GHOST_ROWS) * c->pitch;
         if (use_f64(c) || !c->d_ctab || span >= (1ull << 32)) return false;
+        if (v == 10)   /* D2Q9 with D2Q16 or D2Q36, constants checked, units listed */
+            return c->rtab && c->d_rctr && c->q[0] == 9 && (c->q[1] == 16 || c->q[1] == 36) && !c->rrows_h.empty();
         return v != 8 || c->border_used;
     }
     if (v == 1) return c->tma_ok;
@@ -1044,6 +1148,7 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
             nsm = 0;
         }
         c->red_blocks = lbk::reduce_blocks(c->nx, c->ny, nsm);
+        c->nsm = nsm;
     }
     c->d_part = static_cast<double *>(own(c, sizeof(double) * 4 * c->red_blocks));
     c->d_out = static_cast<double *>(own(c, sizeof(double) * 4));
@@ -1124,6 +1229,11 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
         /* constant tables of layouts 7 / 8 (without them those layouts are not offered) */
         c->d_ctab = own(c, lbk::pair_table_bytes());
         if (c->d_ctab) lbk::launch_pair_table(make_params<float>(c, 0, 1, 0.0), c->d_ctab, c->stream);
+        /* layout 10: the same constants for kernel-parameter space */
+        if (c->d_ctab) {
+            c->rtab.reset(new lbk::RingTab());
+            if (lbk::ring_tab_build(c->d_ctab, c->q, c->rtab.get(), c->stream) != 0) c->rtab.reset();
+        }
     }
     *out = c;
     e = lb_init_equilibrium(c, nullptr, nullptr, nullptr);

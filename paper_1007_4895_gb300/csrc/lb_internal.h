@@ -22,6 +22,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <vector_types.h>
+
 #define LB_GHOST 4
 #define LB_GHOST_ROWS 2
 #define LB_TILE_X 128
@@ -135,8 +137,10 @@ void launch_aux(int store, const StepParams<R> &p, const int2 *list, int n, void
  * per thread in high-order bands), 7 layout 0's threads with paired FP32 arithmetic on
  * the rows without boundary work (lb_pair.cuh; FP32 and 16-bit storage), 8 layout 7
  * with its blocks launched in block_order, 9 layout 7's arithmetic fed by a per-thread
- * ring of asynchronous copies, boundary work in the same kernel (lb_ring.cuh) */
-#define LB_NUM_VARIANTS 10
+ * ring of asynchronous copies, boundary work in the same kernel (lb_ring.cuh), 10 layout
+ * 9's arithmetic in a persistent kernel over row units, most expensive first, with the
+ * rows without boundary work specialised on the velocity set (lb_ring2.cuh) */
+#define LB_NUM_VARIANTS 11
 /* layout 7 / 8: p.block_order selects between them (FP32 and 16-bit storage); p.ctab
  * must hold the tables that launch_pair_table wrote for this lattice */
 void launch_pair(int store, const StepParams<float> &p, void *stream);
@@ -144,6 +148,42 @@ void launch_pair(int store, const StepParams<float> &p, void *stream);
 void launch_ring(int store, const StepParams<float> &p, void *stream);
 size_t pair_table_bytes();
 void launch_pair_table(const StepParams<float> &p, void *dst, void *stream);
+
+/* Layout 10: the per-population constants of one lattice, passed by value in kernel
+ * parameter space (read with a warp-uniform index) */
+struct alignas(16) RingPop {
+    float2 cx2, cy2;      /* (xi_x, xi_x), (xi_y, xi_y) */
+    float2 ncx2, nacy2;   /* (-c_x, -c_x), (-|c_y|, -|c_y|): Courant numbers */
+    float2 ky2, gxi2;     /* ((1 - |c_y|) / 2, ...), (g.xi, g.xi) */
+    float2 w2, winv2;     /* (w, w), (1 / w, 1 / w) */
+    float2 wcx2, wcy2;    /* (w xi_x, ...), (w xi_y, ...) */
+    float kx;             /* (1 - |c_x|) / 2 */
+    int ystep;            /* sign(c_y) x pitch */
+    int pad[2];
+};
+struct RingTab {
+    RingPop pop[2][LB_QMAX];
+};
+/* Fills tab from the tables at d_ctab (launch_pair_table) for sets of q[0], q[1]
+ * populations; synchronises stream. Returns 0, or -1 when a set's populations are not
+ * in the order the layout-10 kernel is specialised on (the product rule, ascending
+ * abscissae) or a copy failed. */
+int ring_tab_build(const void *d_ctab, const int q[2], RingTab *tab, void *stream);
+/* Layout 10: the row queues of one lattice. rows[] holds work items (row << 16 | kind
+ * << 14 | tile; kind 0 lean, 1 edge, 2 general); queue q owns rows[desc[q].x ..
+ * desc[q].x + desc[q].y); queues 0 .. nq - 1 belong to SMs (by %smid modulo nq), queue
+ * nq is shared. ctr[0 .. nq] count the items taken from each queue, ctr[nq + 1] the
+ * warps that have finished; all are zero between launches, and every launch leaves
+ * them so. */
+struct RowQueues {
+    const uint32_t *rows;
+    const int2 *desc;
+    uint32_t *ctr;
+    int nq;
+};
+/* Layout 10 (sets of 9 and of 16 or 36 populations), at most nblocks blocks */
+void launch_ring_units(int store, const StepParams<float> &p, const RingTab &tab, const RowQueues &rq, int nblocks,
+                       void *stream);
 
 /* The quad of nodes x0 .. x0+3 of row j needs none of the boundary work of the step
  * (wall overwrite, ghost-row or ghost-column copies, pressure column, mode-B shadow or

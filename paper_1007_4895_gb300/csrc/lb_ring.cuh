@@ -68,6 +68,91 @@ __device__ __forceinline__ void ring_commit() { asm volatile("cp.async.commit_gr
 template <int N>
 __device__ __forceinline__ void ring_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+/* Sec. 3.2, diffuse wall: f = rho_W S(u_W) for the gas-bound populations of a wall-row
+ * quad (set s, wall 0 bottom / 1 top, nsgn = +1 / -1), with zero net mass flux through
+ * the wall node; num[k] = sum over the wall-bound populations of |xi.n| w d. store(dst,
+ * -1, dv, w) writes four deviations rounded to nearest, with the row's ghost copies. */
+template <int Q, typename T, typename STORE>
+__device__ __forceinline__ void ring_wall_fill(const StepParams<float> &p, int s, int wall, float nsgn,
+                                               const float (&num)[4], T *fout, uint32_t own, const STORE &store)
+{
+    const SetConst<float> &c = p.set[s];
+    const float rho0 = p.rho0;
+    const uint32_t plane = (uint32_t)p.plane;
+    const float uwx = p.uw_x[wall], uwy = p.uw_y[wall];
+    const float usw = uwx * uwx + uwy * uwy;
+    const float kd = p.kdiff[s][wall], kout = p.kout[s][wall];
+    float rwd[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) rwd[k] = fmaf(rho0, kd, num[k]) / kout;   /* rho_W - rho0 */
+#pragma unroll 1
+    for (int a = 0; a < Q; ++a) {
+        if (c.cy[a] * nsgn <= 0.0f) continue;
+        const float ew = c.cx[a] * uwx + c.cy[a] * uwy;
+        const float sm1 = ew + 0.5f * (ew * ew - usw);    /* S / w - 1 */
+        float dv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dv[k] = fmaf(rwd[k] + rho0, sm1, rwd[k]);
+        store(fout + (uint32_t)a * plane + own, -1, dv, c.w[a]);
+    }
+}
+
+/* Sec. 2.2, mode B: the quad x0 .. x0 + 3 of row j (set s, final populations already
+ * stored) rebuilt in the other set from its second-order Hermite coefficients, with the
+ * row's ghost copies (nimg rows at offsets img) and per-node stores where not plain. */
+template <int ST, int Q, bool COL>
+__device__ __forceinline__ void ring_shadow(const StepParams<float> &p, int s, int x0, int j, const bool (&valid)[4],
+                                            bool plain, int nimg, const int (&img)[2], const float (&dl)[8])
+{
+    using T = typename Store<ST>::T;
+    const SetConst<float> &c = p.set[s];
+    const int t = 1 - s;
+    const SetConst<float> &ct = p.set[t];
+    const float rho0 = p.rho0;
+    const uint32_t plane = (uint32_t)p.plane, pitch = (uint32_t)p.pitch;
+    const uint32_t col = (uint32_t)(x0 + LB_GHOST);
+    const uint32_t own = (uint32_t)j * pitch + col;
+    const T *fown = static_cast<const T *>(p.fout[s]);
+    float h[4][6];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int m = 0; m < 6; ++m) h[k][m] = 0.0f;
+#pragma unroll 9
+    for (int a = 0; a < Q; ++a) {
+        T raw[4];
+        ldn<4>(fown + (uint32_t)a * plane + own, raw);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!valid[k]) continue;
+            float d;
+            if constexpr (COL) d = decode_col<ST>(raw[k], c.winv[a], rho0, dl[k + 2]);
+            else d = decode<ST>(raw[k], c.winv[a], rho0);
+            hermite_acc(c, a, d, h[k]);
+        }
+    }
+    T *ftd = static_cast<T *>(p.fout[t]);
+#pragma unroll 4
+    for (int b = 0; b < ct.q; ++b) {
+        T *prow = ftd + (size_t)b * p.plane + (size_t)j * pitch;
+        T e[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float v = hermite_rebuild(ct, b, h[k]);
+            if constexpr (COL) e[k] = encode_col<ST>(v, ct.w[b], rho0, dl[k + 2]);
+            else e[k] = encode<ST>(v, ct.w[b], rho0);
+        }
+        if (plain) {
+            st4(prow + col, e);
+            for (int m = 0; m < nimg; ++m) st4(prow + (ptrdiff_t)img[m] * (ptrdiff_t)pitch + col, e);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (valid[k]) put1r(p, prow, x0 + k, j, e[k]);
+        }
+    }
+}
+
 template <int ST, int Q, bool COL, bool FORCE>
 __device__ __forceinline__ void ring_cells(const StepParams<float> &p, int s, uint8_t flags, int x0, int j,
                                            const PairC *pcs, const PairC2 *pcs2, const MomC2 *mcs,
@@ -244,67 +329,9 @@ __device__ __forceinline__ void ring_cells(const StepParams<float> &p, int s, ui
     }
     ring_wait<0>();
 
-    /* 4. diffuse wall: f = rho_W S(u_W) for the gas-bound populations, with zero net mass
-     * flux through the wall node */
-    if (wall >= 0) {
-        const SetConst<float> &c = p.set[s];
-        const float uwx = p.uw_x[wall], uwy = p.uw_y[wall];
-        const float usw = uwx * uwx + uwy * uwy;
-        const float kd = p.kdiff[s][wall], kout = p.kout[s][wall];
-        float rwd[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) rwd[k] = fmaf(rho0, kd, num[k]) / kout;   /* rho_W - rho0 */
-#pragma unroll 1
-        for (int a = 0; a < Q; ++a) {
-            if (c.cy[a] * nsgn <= 0.0f) continue;
-            const float ew = c.cx[a] * uwx + c.cy[a] * uwy;
-            const float sm1 = ew + 0.5f * (ew * ew - usw);    /* S / w - 1 */
-            float dv[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) dv[k] = fmaf(rwd[k] + rho0, sm1, rwd[k]);
-            store(fout + (uint32_t)a * plane + own, -1, dv, c.w[a]);
-        }
-    }
-
-    /* 5. mode B: this node rebuilt in the other set from its final populations */
-    if (flags & LB_TILE_SHADOW) {
-        const SetConst<float> &c = p.set[s];
-        const int t = 1 - s;
-        const SetConst<float> &ct = p.set[t];
-        float h[4][6];
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-            for (int m = 0; m < 6; ++m) h[k][m] = 0.0f;
-#pragma unroll 9
-        for (int a = 0; a < Q; ++a) {
-            T raw[4];
-            ldn<4>(fout + (uint32_t)a * plane + own, raw);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (valid[k]) hermite_acc(c, a, dec1(raw[k], c.winv[a], k + 2), h[k]);
-        }
-        T *ftd = static_cast<T *>(p.fout[t]);
-#pragma unroll 4
-        for (int b = 0; b < ct.q; ++b) {
-            T *prow = ftd + (size_t)b * p.plane + (size_t)j * pitch;
-            T e[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float v = hermite_rebuild(ct, b, h[k]);
-                if constexpr (COL) e[k] = encode_col<ST>(v, ct.w[b], rho0, dl[k + 2]);
-                else e[k] = encode<ST>(v, ct.w[b], rho0);
-            }
-            if (plain) {
-                st4(prow + col, e);
-                for (int m = 0; m < nimg; ++m) st4(prow + (ptrdiff_t)img[m] * (ptrdiff_t)pitch + col, e);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (valid[k]) put1r(p, prow, x0 + k, j, e[k]);
-            }
-        }
-    }
+    /* 4. diffuse wall, 5. mode-B rebuild */
+    if (wall >= 0) ring_wall_fill<Q>(p, s, wall, nsgn, num, fout, own, store);
+    if (flags & LB_TILE_SHADOW) ring_shadow<ST, Q, COL>(p, s, x0, j, valid, plain, nimg, img, dl);
 }
 
 template <int ST, bool COL, bool FORCE>

@@ -1,0 +1,604 @@
+/*
+ * lb_ring2.cuh -- the ring-fed step of lb_ring.cuh as a persistent kernel over row work
+ * queues (layout 10).
+ *
+ * Work item: one row of one 128-column tile, done by one warp (a quad of nodes per
+ * lane). The host groups the rows in block units of LB_STEP_BY rows of a tile (what a
+ * block of layout 9 does), sorts the units most work first, and deals them round-robin
+ * to one queue per SM, keeping the last (cheapest) tenth in a shared queue. A warp takes
+ * rows from the queue of the SM it runs on, then from the shared queue, then whatever
+ * is left anywhere (so an SM that got fewer blocks loses no work). The warps of an SM
+ * thus work on neighbouring rows of the same tiles and share their stencil rows in L1,
+ * no warp waits for another, and the long high-order rows start first.
+ *
+ * The rows are of four kinds, decided on the host (stochastic rounding makes every row
+ * general):
+ *   - lean: no boundary work (pressure columns count as none: the pressure pass
+ *     overwrites what the step stores there);
+ *   - row: a diffuse wall, ghost-row copies, a mode-B shadow or periodic ghost columns:
+ *     the lean population loop (plus the wall sums of a wall row), then that work;
+ *   - edge: a tile that ends inside the grid's last 128 columns, stored node by node;
+ *   - general: stochastic rounding, or boundary work in such a tile.
+ * Lean, row and edge rows run a body specialised on the velocity set: the loop is
+ * unrolled over the abscissae of the product rule (alpha = iy n + ix), so the sign of
+ * xi_x, whether xi_y is zero and the ring slot of every population are compile-time
+ * constants, and the per-population constants are read from kernel-parameter space
+ * with a warp-uniform index. General rows run the body of layout 9, not inlined.
+ *
+ * The arithmetic is that of layout 9 (lb_pair.cuh), operation for operation, so the
+ * two layouts give the same bits.
+ */
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <type_traits>
+
+#include "lb_ring.cuh"
+
+namespace lbk {
+
+/* sign of abscissa i of the ascending n-point Gauss-Hermite rule (0 at the middle of an
+ * odd rule); the host checks each lattice's sets against it before offering layout 10 */
+__host__ __device__ constexpr int gh_sign(int n, int i) { return (n & 1) && i == n / 2 ? 0 : (i < n / 2 ? -1 : 1); }
+
+/* Row kinds of the queues */
+enum : uint32_t { RING_LEAN = 0u, RING_EDGE = 1u, RING_ROW = 2u, RING_GENERAL = 3u };
+
+/* Dynamic shared memory of a layout-10 block: the ring, then 16 bytes per thread for the
+ * wall sums of a wall row. */
+template <int ST>
+__host__ __device__ constexpr size_t ring_unit_smem_bytes()
+{
+    return ring_smem_bytes<ST>() + (size_t)LB_BX * LB_BY * sizeof(float4);
+}
+
+/* The boundary work of a row of kind RING_ROW (set S of Q populations, the other set of
+ * QT), after the population loop has stored every node of the lane's quad as an inner
+ * node: the diffuse-wall fill (Sec. 3.2; num = sum over the wall-bound populations of
+ * |xi.n| w d, wsgn = +1 bottom wall, -1 top wall), the copies of the row into its ghost
+ * rows and of the lane's nodes into periodic ghost columns, and the mode-B rebuild of a
+ * shadow row in the other set (Sec. 2.2). Loops over populations are unrolled, so every
+ * constant of the velocity sets is an immediate operand. */
+template <int ST, int Q, int S, int QT, bool COL>
+__device__ __forceinline__ void ring_row_finish(const StepParams<float> &p, int x0, int j, uint8_t flags, float wsgn,
+                                                const float4 &num, const float (&dl)[8])
+{
+    using T = typename Store<ST>::T;
+    const SetConst<float> &c = p.set[S];
+    const SetConst<float> &ct = p.set[1 - S];
+    const float rho0 = p.rho0;
+    const uint32_t plane = (uint32_t)p.plane, pitch = (uint32_t)p.pitch;
+    const uint32_t col = (uint32_t)(x0 + LB_GHOST);
+    T *const frow = static_cast<T *>(p.fout[S]) + (size_t)j * pitch;   /* row j of plane 0, column 0 - LB_GHOST */
+    int img[2] = {0, 0};
+    const int nimg = row_images(p, j, img);
+    const bool gx = p.periodic_x && (x0 < LB_GHOST || x0 + 3 >= p.nx - LB_GHOST);
+    const bool shadow = flags & LB_TILE_SHADOW;
+    const int wall = wsgn > 0.0f ? 0 : (wsgn < 0.0f ? 1 : -1);
+    auto enc = [&](float d, float w, int k) -> T {
+        if constexpr (COL) return encode_col<ST>(d, w, rho0, dl[k + 2]);
+        else return encode<ST>(d, w, rho0);
+    };
+    /* quad e of row prow (column 0 - LB_GHOST) into the row itself (self), its ghost rows
+     * and, for this lane's nodes, the periodic ghost columns of each */
+    auto copies = [&](T *prow, const T (&e)[4], bool self) {
+        for (int t = -1; t < nimg; ++t) {
+            T *r = t < 0 ? prow : prow + (ptrdiff_t)img[t] * (ptrdiff_t)pitch;
+            if (t >= 0 || self) st4(r + col, e);
+            if (gx) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int x = x0 + k;
+                    if (x < LB_GHOST) r[x + p.nx + LB_GHOST] = e[k];
+                    if (x >= p.nx - LB_GHOST) r[x - p.nx + LB_GHOST] = e[k];
+                }
+            }
+        }
+    };
+    /* diffuse wall: f = rho_W S(u_W) for the gas-bound populations, zero net mass flux */
+    if (wall >= 0) {
+        const float uwx = p.uw_x[wall], uwy = p.uw_y[wall];
+        const float usw = uwx * uwx + uwy * uwy;
+        const float kd = p.kdiff[S][wall], kout = p.kout[S][wall];
+        const float nm[4] = {num.x, num.y, num.z, num.w};
+        float rwd[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rwd[k] = fmaf(rho0, kd, nm[k]) / kout;   /* rho_W - rho0 */
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            if (c.cy[a] * wsgn <= 0.0f) continue;
+            const float ew = c.cx[a] * uwx + c.cy[a] * uwy;
+            const float sm1 = ew + 0.5f * (ew * ew - usw);    /* S / w - 1 */
+            T e[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) e[k] = enc(fmaf(rwd[k] + rho0, sm1, rwd[k]), c.w[a], k);
+            copies(frow + (size_t)a * plane, e, true);
+        }
+    }
+    if (nimg == 0 && !gx && !shadow) return;
+    /* copies of the populations the loop stored, and the shadow's Hermite coefficients */
+    float h[4][6];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int m = 0; m < 6; ++m) h[k][m] = 0.0f;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        T *prow = frow + (size_t)a * plane;
+        T raw[4];
+        ldn<4>(prow + col, raw);
+        if (!(wall >= 0 && c.cy[a] * wsgn > 0.0f)) copies(prow, raw, false);
+        if (shadow) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float d;
+                if constexpr (COL) d = decode_col<ST>(raw[k], c.winv[a], rho0, dl[k + 2]);
+                else d = decode<ST>(raw[k], c.winv[a], rho0);
+                hermite_acc(c, a, d, h[k]);
+            }
+        }
+    }
+    if (!shadow) return;
+    T *const trow = static_cast<T *>(p.fout[1 - S]) + (size_t)j * pitch;
+#pragma unroll
+    for (int b = 0; b < QT; ++b) {
+        T e[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) e[k] = enc(hermite_rebuild(ct, b, h[k]), ct.w[b], k);
+        copies(trow + (size_t)b * plane, e, true);
+    }
+}
+
+/* One row of set S of Q = n^2 populations (n = 3, 4 or 6; the other set has QT) of kind
+ * KIND, the quad of nodes x0 .. x0 + 3 of this lane (x0 < nx). Lean and row kinds store
+ * every node as an inner node (a pressure node is then overwritten by the pressure pass,
+ * with its ghost columns, images and shadow); the row kind then does its boundary work
+ * (ring_row_finish); the edge kind stores node by node (ragged end, periodic ghost
+ * columns). */
+template <int ST, int Q, int S, int QT, bool COL, bool FORCE, uint32_t KIND>
+__device__ __forceinline__ void ring_lean(const StepParams<float> &p, const RingTab &tab, int x0, int j,
+                                          uint8_t flags, unsigned char *ring)
+{
+    constexpr bool ROW = KIND == RING_ROW;
+    constexpr bool EDGE = KIND == RING_EDGE;   /* lanes store node by node */
+    using T = typename Store<ST>::T;
+    constexpr int N = Q == 9 ? 3 : (Q == 16 ? 4 : 6);
+    constexpr int NT = LB_BX * LB_BY;
+    constexpr int C4 = 4 * (int)sizeof(T), C2 = 2 * (int)sizeof(T);
+    constexpr size_t STAGE = ring_stage_bytes<ST>();
+    const RingPop *tp = tab.pop[S];
+    const int tid = threadIdx.x;
+    /* edge kind: nodes this lane stores one by one (pressure column, beyond nx, periodic
+     * ghost-column images) */
+    bool valid[4] = {true, true, true, true};
+    bool plain = true;
+    if constexpr (EDGE) {
+        plain = !(p.periodic_x && (x0 < LB_GHOST || x0 + 3 >= p.nx - LB_GHOST));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            valid[k] = x0 + k < p.nx && !is_pressure_node(p, x0 + k, j);
+            plain = plain && valid[k];
+        }
+    }
+    /* row kind: the wall of a diffuse-wall row (+1 bottom, -1 top, 0 none) and the lane's
+     * wall sums in shared memory after the ring */
+    float wsgn = 0.0f;
+    if constexpr (ROW) {
+        if (j == 0 && p.wall_diffuse[0]) wsgn = 1.0f;
+        if (j == p.ny - 1 && p.wall_diffuse[1]) wsgn = -1.0f;
+    }
+    float4 *const numslot = reinterpret_cast<float4 *>(ring + ring_smem_bytes<ST>()) + tid;
+    if constexpr (ROW) *numslot = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const T *__restrict__ fin = static_cast<const T *>(p.fin[S]);
+    T *__restrict__ fout = static_cast<T *>(p.fout[S]);
+    const uint32_t plane = (uint32_t)p.plane, pitch = (uint32_t)p.pitch;
+    const uint32_t col = (uint32_t)(x0 + LB_GHOST);
+    const uint32_t own = (uint32_t)j * pitch + col;
+    const float rho0 = p.rho0;
+    const float2 nrho02 = f2(-rho0);
+    /* per-column reference density: delta at columns x0 - 2 .. x0 + 5 */
+    float dl[8];
+    if constexpr (COL) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) dl[i] = p.dcol[col - 2 + i];
+    }
+    unsigned char *const mine4 = ring + (size_t)tid * C4;
+    unsigned char *const mine2 = ring + (size_t)4 * NT * C4 + (size_t)tid * C2;
+    /* copies of population b into ring stage b % 3 (HX: xi_x != 0, HY: xi_y != 0) */
+    auto issue = [&](int b, auto hx, auto hy, auto stage) {
+        constexpr int st = decltype(stage)::value;
+        const T *pa = fin + (uint32_t)b * plane + own;
+        unsigned char *s4 = mine4 + st * STAGE;
+        unsigned char *s2 = mine2 + st * STAGE;
+        ring_cp<C4>(s4, pa);
+        if constexpr (decltype(hy)::value) {
+            const int ys = tp[b].ystep;
+            ring_cp<C4>(s4 + (size_t)NT * C4, pa - 2 * ys);
+            ring_cp<C4>(s4 + (size_t)2 * NT * C4, pa - ys);
+            ring_cp<C4>(s4 + (size_t)3 * NT * C4, pa + ys);
+        }
+        if constexpr (decltype(hx)::value) {
+            ring_cp<C2>(s2, pa - 2);
+            ring_cp<C2>(s2 + (size_t)NT * C2, pa + 4);
+        }
+    };
+    using I0 = std::integral_constant<int, 0>;
+    using I1 = std::integral_constant<int, 1>;
+    using BT = std::true_type;
+    using BF = std::false_type;
+    /* populations 0 and 1 */
+    if constexpr (N == 3) {
+        issue(0, BT{}, BT{}, I0{});   /* (-, -) */
+        ring_commit();
+        issue(1, BF{}, BT{}, I1{});   /* (0, -) */
+        ring_commit();
+    } else {
+        issue(0, BT{}, BT{}, I0{});
+        ring_commit();
+        issue(1, BT{}, BT{}, I1{});
+        ring_commit();
+    }
+
+    auto dec2 = [&](float2 raw, float2 winv2, int k) -> float2 {
+        if constexpr (ST == 1) return fma2(raw, winv2, nrho02);
+        else if constexpr (COL) return add2(raw, make_float2(dl[k + 2], dl[k + 3]));
+        else return raw;
+    };
+    auto dec1 = [&](T raw, float winv, int i) -> float {
+        if constexpr (COL) return decode_col<ST>(raw, winv, rho0, dl[i]);
+        else return decode<ST>(raw, winv, rho0);
+    };
+
+    /* 1. moments */
+    float2 rd[2] = {f2(0.0f), f2(0.0f)}, jx[2] = {f2(0.0f), f2(0.0f)}, jy[2] = {f2(0.0f), f2(0.0f)};
+#pragma unroll (Q == 36 ? 6 : Q)
+    for (int a = 0; a < Q; ++a) {
+        const RingPop &rp = tp[a];
+        float2 v[2];
+        pair_ld<ST>(fin + (uint32_t)a * plane + own, v[0], v[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float2 d = dec2(v[h], rp.winv2, 2 * h);
+            rd[h] = fma2(rp.w2, d, rd[h]);
+            jx[h] = fma2(rp.wcx2, d, jx[h]);
+            jy[h] = fma2(rp.wcy2, d, jy[h]);
+        }
+    }
+    const PairNode nd = pair_node_state<FORCE>(p, rd, jx, jy);
+
+    /* 2. populations: a = iy N + ix, stage a % 3 */
+    auto body = [&](int a, auto sxc, auto hyc, auto stc, int b, auto bhx, auto bhy, auto bst, bool more) {
+        constexpr int SX = decltype(sxc)::value;
+        constexpr bool HY = decltype(hyc)::value;
+        constexpr int st = decltype(stc)::value;
+        ring_wait<RING_STAGES - 2>();
+        const RingPop &rp = tp[a];
+        T own_v[4], yv[3][4], hl[2], hr[2];
+        const unsigned char *s4 = mine4 + st * STAGE;
+        const unsigned char *s2 = mine2 + st * STAGE;
+        ldn<4>(reinterpret_cast<const T *>(s4), own_v);
+        if constexpr (HY) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) ldn<4>(reinterpret_cast<const T *>(s4 + (size_t)(1 + i) * NT * C4), yv[i]);
+        }
+        if constexpr (SX != 0) {
+            ld2(reinterpret_cast<const T *>(s2), hl);
+            ld2(reinterpret_cast<const T *>(s2 + (size_t)NT * C2), hr);
+        }
+        if (more) issue(b, bhx, bhy, bst);
+        ring_commit();
+        float2 v[2], c[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) v[h] = dec2(make_float2(to_r(own_v[2 * h]), to_r(own_v[2 * h + 1])), rp.winv2, 2 * h);
+        /* collision and force */
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float2 eu;
+            if constexpr (SX == 0 && !HY) eu = f2(0.0f);
+            else if constexpr (SX == 0) eu = mul2(rp.cy2, nd.uy[h]);
+            else if constexpr (!HY) eu = mul2(rp.cx2, nd.ux[h]);
+            else eu = fma2(rp.cy2, nd.uy[h], mul2(rp.cx2, nd.ux[h]));
+            const float2 t = fma2(mul2(f2(0.5f), eu), eu, eu);
+            c[h] = fma2(nd.nom[h], v[h], fma2(nd.P[h], t, nd.B[h]));
+            if constexpr (FORCE) c[h] = fma2(nd.dr[h], fma2(rp.gxi2, eu, rp.gxi2), c[h]);
+        }
+        /* x flux, upwind side by the sign of xi_x */
+        if constexpr (SX != 0) {
+            const float vv[4] = {v[0].x, v[0].y, v[1].x, v[1].y};
+            const float winv = rp.winv2.x;
+            const float l0 = dec1(hl[0], winv, 0), l1 = dec1(hl[1], winv, 1);
+            const float r0 = dec1(hr[0], winv, 6), r1 = dec1(hr[1], winv, 7);
+            const float kx = rp.kx;
+            float Dx[4];
+            if constexpr (SX > 0) {
+                float d[6], n[6], m[5];
+                d[0] = l1 - l0;
+                d[1] = vv[0] - l1;
+                d[2] = vv[1] - vv[0];
+                d[3] = vv[2] - vv[1];
+                d[4] = vv[3] - vv[2];
+                d[5] = r0 - vv[3];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) n[i] = neg_part(d[i]);
+#pragma unroll
+                for (int i = 0; i < 5; ++i) m[i] = minmod_n(d[i], d[i + 1], n[i], n[i + 1]);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) Dx[k] = fmaf(kx, m[k + 1] - m[k], d[k + 1]);
+                (void)r1;
+            } else {
+                float e[6], n[6], m[5];
+                e[0] = vv[0] - l1;
+                e[1] = vv[1] - vv[0];
+                e[2] = vv[2] - vv[1];
+                e[3] = vv[3] - vv[2];
+                e[4] = r0 - vv[3];
+                e[5] = r1 - r0;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) n[i] = neg_part(e[i]);
+#pragma unroll
+                for (int i = 0; i < 5; ++i) m[i] = minmod_n(e[i], e[i + 1], n[i], n[i + 1]);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) Dx[k] = fmaf(-kx, m[k + 1] - m[k], e[k + 1]);
+                (void)l0;
+            }
+            c[0] = fma2(rp.ncx2, make_float2(Dx[0], Dx[1]), c[0]);
+            c[1] = fma2(rp.ncx2, make_float2(Dx[2], Dx[3]), c[1]);
+        }
+        /* y flux on the sign-reflected window (rows j - 2s, j - s, j, j + s) */
+        if constexpr (HY) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float2 w0 = dec2(make_float2(to_r(yv[0][2 * h]), to_r(yv[0][2 * h + 1])), rp.winv2, 2 * h);
+                const float2 w1 = dec2(make_float2(to_r(yv[1][2 * h]), to_r(yv[1][2 * h + 1])), rp.winv2, 2 * h);
+                const float2 w3 = dec2(make_float2(to_r(yv[2][2 * h]), to_r(yv[2][2 * h + 1])), rp.winv2, 2 * h);
+                const float2 d0 = sub2(w1, w0), d1 = sub2(v[h], w1), d2 = sub2(w3, v[h]);
+                float2 ma, mb;
+                {
+                    const float lo = fminf(d1.x, 0.0f), hi = fmaxf(d1.x, 0.0f);
+                    ma.x = fminf(fmaxf(d0.x, lo), hi);
+                    mb.x = fminf(fmaxf(d2.x, lo), hi);
+                }
+                {
+                    const float lo = fminf(d1.y, 0.0f), hi = fmaxf(d1.y, 0.0f);
+                    ma.y = fminf(fmaxf(d0.y, lo), hi);
+                    mb.y = fminf(fmaxf(d2.y, lo), hi);
+                }
+                const float2 Dy = fma2(rp.ky2, sub2(mb, ma), d1);
+                c[h] = fma2(rp.nacy2, Dy, c[h]);
+            }
+        }
+        float2 dn[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) dn[h] = add2(v[h], c[h]);
+        T *dst = fout + (uint32_t)a * plane + own;
+        if constexpr (ROW) {
+            /* wall row: the wall-bound populations' |xi.n| w d, summed in population order */
+            const float xn = rp.cy2.x * wsgn;
+            if (xn < 0.0f) {
+                const float cw = -xn * rp.w2.x;
+                float4 n = *numslot;
+                n.x = fmaf(cw, dn[0].x, n.x);
+                n.y = fmaf(cw, dn[0].y, n.y);
+                n.z = fmaf(cw, dn[1].x, n.z);
+                n.w = fmaf(cw, dn[1].y, n.w);
+                *numslot = n;
+            }
+        }
+        if (!EDGE || plain) {
+            if constexpr (ST == 1) {
+                pair_st<ST>(dst, mul2(rp.w2, add2(f2(rho0), dn[0])), mul2(rp.w2, add2(f2(rho0), dn[1])));
+            } else if constexpr (COL) {
+                pair_st<ST>(dst, sub2(dn[0], make_float2(dl[2], dl[3])), sub2(dn[1], make_float2(dl[4], dl[5])));
+            } else {
+                pair_st<ST>(dst, dn[0], dn[1]);
+            }
+        } else {
+            const float dv[4] = {dn[0].x, dn[0].y, dn[1].x, dn[1].y};
+            T *prow = dst - col;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (!valid[k]) continue;
+                T e;
+                if constexpr (COL) e = encode_col<ST>(dv[k], rp.w2.x, rho0, dl[k + 2]);
+                else e = encode<ST>(dv[k], rp.w2.x, rho0);
+                put1(p, prow, x0 + k, e);
+            }
+        }
+    };
+
+    if constexpr (N == 3) {
+        /* D2Q9, fully unrolled: (sx, sy) of a = 3 iy + ix is (ix - 1, iy - 1) */
+        using IM = std::integral_constant<int, -1>;
+        using IZ = std::integral_constant<int, 0>;
+        using IP = std::integral_constant<int, 1>;
+        using I2 = std::integral_constant<int, 2>;
+        body(0, IM{}, BT{}, I0{}, 2, BT{}, BT{}, I2{}, true);
+        body(1, IZ{}, BT{}, I1{}, 3, BT{}, BF{}, I0{}, true);
+        body(2, IP{}, BT{}, I2{}, 4, BF{}, BF{}, I1{}, true);
+        body(3, IM{}, BF{}, I0{}, 5, BT{}, BF{}, I2{}, true);
+        body(4, IZ{}, BF{}, I1{}, 6, BT{}, BT{}, I0{}, true);
+        body(5, IP{}, BF{}, I2{}, 7, BF{}, BT{}, I1{}, true);
+        body(6, IM{}, BT{}, I0{}, 8, BT{}, BT{}, I2{}, true);
+        body(7, IZ{}, BT{}, I1{}, 0, BT{}, BT{}, I0{}, false);
+        body(8, IP{}, BT{}, I2{}, 0, BT{}, BT{}, I0{}, false);
+    } else {
+        /* product sets of even n: every xi_x and xi_y nonzero, sign(xi_x) = sign by ix */
+        static_assert(Q % RING_STAGES == 0 || Q == 16, "ring stages");
+#pragma unroll (N == 6 ? 1 : N)
+        for (int iy = 0; iy < N; ++iy) {
+            const int a0 = iy * N;
+            const bool last = iy == N - 1;
+            auto sxof = [](auto ixc) { return std::integral_constant<int, gh_sign(N, decltype(ixc)::value)>{}; };
+            auto one = [&](auto ixc) {
+                constexpr int ix = decltype(ixc)::value;
+                /* stage of a = a0 + ix: a0 % 3 is 0 for n = 6; for n = 4 the loop is unrolled */
+                const int a = a0 + ix;
+                const bool more = !(last && ix + 2 >= N);
+                if constexpr (N == 6) {
+                    body(a, sxof(ixc), BT{}, std::integral_constant<int, ix % 3>{}, a + 2, BT{}, BT{},
+                         std::integral_constant<int, (ix + 2) % 3>{}, more);
+                } else {
+                    /* n = 4: iy is a compile-time constant after unrolling only in value,
+                     * so the stage comes from a runtime-uniform a; dispatch on it */
+                    const int st = a % 3;
+                    if (st == 0) body(a, sxof(ixc), BT{}, I0{}, a + 2, BT{}, BT{}, std::integral_constant<int, 2>{}, more);
+                    else if (st == 1) body(a, sxof(ixc), BT{}, I1{}, a + 2, BT{}, BT{}, I0{}, more);
+                    else body(a, sxof(ixc), BT{}, std::integral_constant<int, 2>{}, a + 2, BT{}, BT{}, I1{}, more);
+                }
+            };
+            one(std::integral_constant<int, 0>{});
+            one(std::integral_constant<int, 1>{});
+            one(std::integral_constant<int, 2>{});
+            one(std::integral_constant<int, 3>{});
+            if constexpr (N == 6) {
+                one(std::integral_constant<int, 4>{});
+                one(std::integral_constant<int, 5>{});
+            }
+        }
+    }
+    ring_wait<0>();
+    if constexpr (ROW) ring_row_finish<ST, Q, S, QT, COL>(p, x0, j, flags, wsgn, *numslot, dl);
+}
+
+/* general units (boundary work, stochastic rounding): the body of layout 9, not inlined,
+ * so that its register demand does not weigh on the lean bodies */
+template <int ST, bool COL, bool FORCE>
+__device__ __noinline__ void ring_general(const StepParams<float> &p, int s, uint8_t flags, int x0, int j, unsigned char *ring)
+{
+    const PairTables *tab = static_cast<const PairTables *>(p.ctab);
+    const int q = p.set[s].q;
+    if (q == 9) ring_cells<ST, 9, COL, FORCE>(p, s, flags, x0, j, tab->pp[s], tab->pp2[s], tab->pm[s], ring);
+    else if (q == 16) ring_cells<ST, 16, COL, FORCE>(p, s, flags, x0, j, tab->pp[s], tab->pp2[s], tab->pm[s], ring);
+    else ring_cells<ST, 36, COL, FORCE>(p, s, flags, x0, j, tab->pp[s], tab->pp2[s], tab->pm[s], ring);
+}
+
+__device__ __forceinline__ uint32_t ring_smid()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+
+/* Sets of D2Q9 (set 0) and Q1 = 16 or 36 populations (set 1). */
+template <int ST, bool COL, bool FORCE, int Q1>
+__global__ void __launch_bounds__(LB_BX *LB_BY, RING_MIN_BLOCKS)
+    ring_unit_kernel(const __grid_constant__ StepParams<float> p, const __grid_constant__ RingTab tab,
+                     const RowQueues rq)
+{
+    extern __shared__ __align__(16) unsigned char ring_smem[];
+    constexpr uint32_t EMPTY = 0xffffffffu;
+    const uint32_t lane = threadIdx.x & 31u;
+    const int nq = rq.nq;
+    /* phase 0: this SM's queue; 1: the shared queue; 2: leftovers of every SM queue */
+    int phase = 0;
+    const int own = (int)(ring_smid() % (uint32_t)nq);
+    for (;;) {
+        uint32_t item = EMPTY;
+        while (phase < 3) {
+            int q = -1;
+            if (phase == 0) {
+                q = own;
+            } else if (phase == 1) {
+                q = nq;
+            } else {
+                /* lanes look at 32 queues at a time; the first with items left is tried */
+                for (int base = 0; base < nq && q < 0; base += 32) {
+                    const int qq = base + (int)lane;
+                    const bool left = qq < nq && __ldcg(rq.ctr + qq) < (uint32_t)rq.desc[qq].y;
+                    const uint32_t m = __ballot_sync(0xffffffffu, left);
+                    if (m) q = base + __ffs(m) - 1;
+                }
+                if (q < 0) {
+                    phase = 3;
+                    break;
+                }
+            }
+            uint32_t t = 0;
+            if (lane == 0) t = atomicAdd(rq.ctr + q, 1u);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            const int2 d = rq.desc[q];
+            if (t < (uint32_t)d.y) {
+                item = rq.rows[d.x + t];
+                break;
+            }
+            if (phase < 2) ++phase;   /* this queue is used up (phase 2 looks again) */
+        }
+        if (item == EMPTY) break;
+        const int tx = (int)(item & 0x3fffu), j = (int)(item >> 16);
+        const uint32_t kind = (item >> 14) & 3u;
+        const uint8_t flags = p.tmap[(size_t)j * p.ntx + tx];
+        const int s = flags & LB_TILE_HIGH;
+        const int x0 = tx * LB_TILE_X + (int)lane * 4;
+        if (kind == RING_LEAN) {
+            if (s == 0) ring_lean<ST, 9, 0, Q1, COL, FORCE, RING_LEAN>(p, tab, x0, j, flags, ring_smem);
+            else ring_lean<ST, Q1, 1, 9, COL, FORCE, RING_LEAN>(p, tab, x0, j, flags, ring_smem);
+        } else if (kind == RING_ROW) {
+            if (s == 0) ring_lean<ST, 9, 0, Q1, COL, FORCE, RING_ROW>(p, tab, x0, j, flags, ring_smem);
+            else ring_lean<ST, Q1, 1, 9, COL, FORCE, RING_ROW>(p, tab, x0, j, flags, ring_smem);
+        } else if (x0 < p.nx) {
+            if (kind == RING_GENERAL) ring_general<ST, COL, FORCE>(p, s, flags, x0, j, ring_smem);
+            else if (s == 0) ring_lean<ST, 9, 0, Q1, COL, FORCE, RING_EDGE>(p, tab, x0, j, flags, ring_smem);
+            else ring_lean<ST, Q1, 1, 9, COL, FORCE, RING_EDGE>(p, tab, x0, j, flags, ring_smem);
+        }
+        __syncwarp();
+    }
+    /* the last warp out zeroes the counters for the next launch */
+    uint32_t done = 0;
+    if (lane == 0) {
+        __threadfence();
+        done = atomicAdd(rq.ctr + nq + 1, 1u);
+    }
+    done = __shfl_sync(0xffffffffu, done, 0);
+    if (done == gridDim.x * (blockDim.x >> 5) - 1u) {
+        for (int k = (int)lane; k <= nq + 1; k += 32) rq.ctr[k] = 0u;
+        __threadfence();
+    }
+}
+
+template <int ST, bool COL, bool FORCE, int Q1>
+void ring_unit_launch(const StepParams<float> &p, const RingTab &tab, const RowQueues &rq, int nblocks,
+                      cudaStream_t st)
+{
+    constexpr size_t smem = ring_unit_smem_bytes<ST>();
+    /* per device: the raised shared-memory limit and the resident blocks of the GPU */
+    static std::atomic<int> resident[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    dev &= 63;
+    int nb = resident[dev].load();
+    if (nb == 0) {
+        auto kern = ring_unit_kernel<ST, COL, FORCE, Q1>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0, nsm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LB_BX * LB_BY, smem);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        nb = std::max(1, per_sm) * std::max(1, nsm);
+        resident[dev].store(nb);
+    }
+    const int grid = std::min(nb, nblocks);
+    if (grid <= 0) return;
+    ring_unit_kernel<ST, COL, FORCE, Q1><<<grid, LB_BX * LB_BY, smem, st>>>(p, tab, rq);
+}
+
+/* layout 10 for one storage format and high-order set size */
+template <int ST, int Q1>
+void launch_ring_units_store(const StepParams<float> &p, const RingTab &tab, const RowQueues &rq, int nblocks,
+                             void *stream)
+{
+    static_assert(ST >= 1 && ST <= 4, "paired FP32 arithmetic: FP32 and 16-bit storage");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if constexpr (Store<ST>::dev) {
+        if (p.dcol) {
+            if (p.has_force) ring_unit_launch<ST, true, true, Q1>(p, tab, rq, nblocks, st);
+            else ring_unit_launch<ST, true, false, Q1>(p, tab, rq, nblocks, st);
+            return;
+        }
+    }
+    if (p.has_force) ring_unit_launch<ST, false, true, Q1>(p, tab, rq, nblocks, st);
+    else ring_unit_launch<ST, false, false, Q1>(p, tab, rq, nblocks, st);
+}
+
+}  // namespace lbk

@@ -1,0 +1,48 @@
+/* Layout-10 step kernel (the ring-fed step as a persistent kernel over row queues) for
+ * one storage format and one high-order set size (one translation unit each, so that
+ * they compile in parallel). */
+#include "lb_ring2.cuh"
+
+namespace lbk {
+template void launch_ring_units_store<2, 36>(const StepParams<float> &, const RingTab &, const RowQueues &,
+                                              int, void *);
+}
+
+namespace lbk {
+int ring_tab_build(const void *d_ctab, const int q[2], RingTab *tab, void *stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PairTables *h = new PairTables;
+    const bool ok = cudaMemcpyAsync(h, d_ctab, sizeof(PairTables), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                    cudaStreamSynchronize(st) == cudaSuccess;
+    int rc = ok ? 0 : -1;
+    auto sgn_f = [](float v) { return v > 0.0f ? 1 : (v < 0.0f ? -1 : 0); };
+    auto sgn_i = [](int v) { return v > 0 ? 1 : (v < 0 ? -1 : 0); };
+    for (int s = 0; s < 2 && rc == 0; ++s) {
+        const int n = q[s] == 9 ? 3 : (q[s] == 16 ? 4 : (q[s] == 36 ? 6 : 0));
+        if (n == 0) rc = -1;
+        for (int a = 0; a < LB_QMAX && rc == 0; ++a) {
+            const PairC &pc = h->pp[s][a];
+            const PairC2 &p2 = h->pp2[s][a];
+            const MomC2 &pm = h->pm[s][a];
+            if (a < q[s] && (sgn_f(pc.crx) != gh_sign(n, a % n) || sgn_i(pc.ystep) != gh_sign(n, a / n))) rc = -1;
+            RingPop &r = tab->pop[s][a];
+            r.cx2 = pc.cx2;
+            r.cy2 = pc.cy2;
+            r.ncx2 = pc.ncx2;
+            r.nacy2 = pc.nacy2;
+            r.ky2 = pc.ky2;
+            r.gxi2 = p2.gxi2;
+            r.w2 = p2.w2;
+            r.winv2 = p2.winv2;
+            r.wcx2 = pm.wcx2;
+            r.wcy2 = pm.wcy2;
+            r.kx = pc.kx;
+            r.ystep = pc.ystep;
+            r.pad[0] = r.pad[1] = 0;
+        }
+    }
+    delete h;
+    return rc;
+}
+}  // namespace lbk

@@ -22,6 +22,9 @@ template <int ST>
 void launch_pair_store(const StepParams<float> &p, void *stream);
 template <int ST>
 void launch_ring_store(const StepParams<float> &p, void *stream);
+template <int ST, int Q1>
+void launch_ring_units_store(const StepParams<float> &p, const RingTab &tab, const RowQueues &rq, int nblocks,
+                             void *stream);
 
 /* ---------------------------------------------------------------- mode A -- */
 
@@ -343,6 +346,19 @@ void launch_ring(int store, const StepParams<float> &p, void *stream)
         case 2: launch_ring_store<2>(p, stream); break;
         case 3: launch_ring_store<3>(p, stream); break;
         case 4: launch_ring_store<4>(p, stream); break;
+        default: break;
+    }
+}
+
+void launch_ring_units(int store, const StepParams<float> &p, const RingTab &tab, const RowQueues &rq, int nblocks,
+                       void *stream)
+{
+    const bool q36 = p.set[1].q == 36;
+    switch (store) {
+        case 1: (q36 ? launch_ring_units_store<1, 36> : launch_ring_units_store<1, 16>)(p, tab, rq, nblocks, stream); break;
+        case 2: (q36 ? launch_ring_units_store<2, 36> : launch_ring_units_store<2, 16>)(p, tab, rq, nblocks, stream); break;
+        case 3: (q36 ? launch_ring_units_store<3, 36> : launch_ring_units_store<3, 16>)(p, tab, rq, nblocks, stream); break;
+        case 4: (q36 ? launch_ring_units_store<4, 36> : launch_ring_units_store<4, 16>)(p, tab, rq, nblocks, stream); break;
         default: break;
     }
 }

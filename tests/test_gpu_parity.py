@@ -9,7 +9,7 @@ from the unit roundoff of the stored deviation (2^-11, 2^-8) times its magnitude
 import numpy as np
 import pytest
 
-from lbinputs import Workload, band_map, couette, long_channel, oscillatory_couette, poiseuille
+from lbinputs import Workload, band_map, couette, long_channel, long_channel_density, oscillatory_couette, poiseuille
 
 from gpu_pair import field_errors, make_pair, population_error
 
@@ -132,7 +132,7 @@ def test_oscillating_wall_fp64():
     assert max(errs.values()) < F64_TOL, errs
 
 
-LAYOUTS = [0, 1, 2, 3, 4, 5, 6, 7, 8, 9]
+LAYOUTS = [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10]
 
 
 @pytest.mark.parametrize("variant", LAYOUTS)
@@ -142,7 +142,7 @@ def test_every_kernel_layout_matches_oracle(variant):
     reproduce the oracle."""
     w = ragged_workload()
     for store, tol in (("f64", F64_TOL), ("f32_dev", 1e-6), ("f32", 1e-4)):
-        if store == "f64" and variant in (1, 4, 7, 8, 9):   # FP32 / 16-bit storage only
+        if store == "f64" and variant in (1, 4, 7, 8, 9, 10):   # FP32 / 16-bit storage only
             continue
         lat, o, eff, got, ref = run_both(w, store, 60, variant=variant)
         assert lat.info()["variant"] == variant
@@ -214,7 +214,7 @@ def _col_pair(w, store, rho0_col, **kw):
     return a, b, o
 
 
-@pytest.mark.parametrize("variant", [0, 7, 9])
+@pytest.mark.parametrize("variant", [0, 7, 9, 10])
 @pytest.mark.parametrize("store", ["f32_dev", "f16_dev", "bf16_dev"])
 @pytest.mark.parametrize("case", ["ragged", "pressure_channel"])
 def test_constant_per_column_reference_changes_nothing(store, case, variant):
@@ -407,11 +407,11 @@ def test_register_block_layouts_equal_quad_layout(store, variant):
         assert np.array_equal(a.populations(s), b.populations(s)), (store, variant, s)
 
 
-@pytest.mark.parametrize("variant", [7, 8, 9])
+@pytest.mark.parametrize("variant", [7, 8, 9, 10])
 @pytest.mark.parametrize("store", ["f32_dev", "f32", "f16_dev", "bf16_dev_sr", "f16_dev_sr"])
 @pytest.mark.parametrize("case", ["ragged", "pressure_channel", "bands_paper", "periodic_box"])
 def test_paired_layout_agrees_with_quad_layout(store, case, variant):
-    """Layouts 7, 8 and 9 fold the collision into per-node coefficients, compute node pairs
+    """Layouts 7 to 10 fold the collision into per-node coefficients, compute node pairs
     with packed FP32 instructions and are built with multiply-add contraction, so they
     round differently from layout 0; the update is the same (stencil, walls, shadows,
     ghost copies, pressure columns, random bits). After 40 steps the two agree to
@@ -441,6 +441,43 @@ def test_paired_layout_agrees_with_quad_layout(store, case, variant):
     errs = field_errors(b.moments(), a.moments())
     tol = {"f32_dev": 1e-6, "f32": 1e-5, "bf16_dev": 3e-2, "f16_dev": 4e-3}[st]
     assert errs["u"] < tol and errs["rho"] < tol, (store, case, errs)
+
+
+@pytest.mark.parametrize("store", ["f32_dev", "f32", "f16_dev", "bf16_dev", "f32_dev_col", "f16_dev_sr"])
+@pytest.mark.parametrize("case", ["ragged", "pressure_channel", "bands_paper", "periodic_box", "sets_9_16"])
+def test_row_unit_layout_equals_ring_layout(store, case):
+    """Layout 10 runs layout 9's arithmetic on rows without boundary work from bodies
+    specialised on the velocity set, and layout 9's own body on the other rows, in a
+    persistent kernel that takes row units from a counter: the same bits as layout 9
+    after an odd and an even number of steps (a unit done twice, skipped, or run with a
+    population's sign pattern wrong would show)."""
+    import paper_1007_4895_gb300 as lb
+    rnd = "stochastic" if store.endswith("_sr") else "nearest"
+    st = store.replace("_sr", "").replace("_col", "")
+    if case == "ragged":
+        w = ragged_workload()
+    elif case == "pressure_channel":
+        w = long_channel(nx=300, ny=37)
+    elif case == "bands_paper":
+        w = couette(nx=200, ny=32, rows=4, kn=0.1, u_wall_lat=0.05, iface="paper")
+    elif case == "sets_9_16":
+        w = long_channel(nx=520, ny=40, sets=(9, 16))
+    else:
+        w = Workload(name="box", nx=260, ny=22, region_map=band_map(260, 22, 3, 0), kn_ref=0.05, gx=1e-3,
+                     walls={"bottom": {"kind": "periodic"}, "top": {"kind": "periodic"}},
+                     init=ragged_workload(nx=260, ny=22).init)
+    kw = {}
+    if store.endswith("_col"):
+        kw["rho0_col"] = long_channel_density(w.nx, 2.0, 1.0) if case in ("pressure_channel", "sets_9_16") \
+            else np.full(w.nx, w.rho0)
+    a = lb.Lattice.from_workload(w, store=st, variant=9, rounding=rnd, **kw)
+    b = lb.Lattice.from_workload(w, store=st, variant=10, rounding=rnd, **kw)
+    assert a.info()["variant"] == 9 and b.info()["variant"] == 10
+    for n in (7, 8):
+        a.step(n)
+        b.step(n)
+        for s in (0, 1):
+            assert np.array_equal(a.populations(s), b.populations(s)), (store, case, n, s)
 
 
 @pytest.mark.parametrize("store", ["f32_dev", "f32", "f16_dev"])
