@@ -356,9 +356,9 @@ int finalize_level_t(lb_ctx *c, int level)
     if (c->opts.iface == LB_IFACE_HERMITE) lbk::launch_shadows<R>(c->store, p, st);
     lbk::launch_iface<R>(c->store, p, st);
     lbk::launch_pressure<R>(c->store, p, st);
-    /* carried moments of this level: read only by layout 4 (and by the autotuner,
-     * which runs while no layout is chosen yet) */
-    if (c->variant < 0 || c->variant == 4) lbk::launch_aux<R>(c->store, p, nullptr, 0, st);
+    /* carried moments of this level: read only by layouts 4 and 10 (and by the
+     * autotuner, which runs while no layout is chosen yet) */
+    if (c->variant < 0 || c->variant == 4 || c->variant == 10) lbk::launch_aux<R>(c->store, p, nullptr, 0, st);
     return launch_check(c, "finalize");
 }
 
@@ -1232,7 +1232,8 @@ int lb_create(const lb_grid *grid, const uint8_t *region_map, const int32_t sets
         /* layout 10: the same constants for kernel-parameter space */
         if (c->d_ctab) {
             c->rtab.reset(new lbk::RingTab());
-            if (lbk::ring_tab_build(c->d_ctab, c->q, c->rtab.get(), c->stream) != 0) c->rtab.reset();
+            if (lbk::ring_tab_build(c->d_ctab, make_params<float>(c, 0, 1, 0.0), c->rtab.get(), c->stream) != 0)
+                c->rtab.reset();
         }
     }
     *out = c;

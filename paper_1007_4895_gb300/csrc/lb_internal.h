@@ -159,16 +159,17 @@ struct alignas(16) RingPop {
     float2 wcx2, wcy2;    /* (w xi_x, ...), (w xi_y, ...) */
     float kx;             /* (1 - |c_x|) / 2 */
     int ystep;            /* sign(c_y) x pitch */
-    int pad[2];
+    float wxx, wxy, wyy;  /* w (xi_x^2 - 1), w xi_x xi_y, w (xi_y^2 - 1) */
+    float hxx, hxy, hyy;  /* (xi_x^2 - 1) / 2, xi_x xi_y, (xi_y^2 - 1) / 2 */
 };
 struct RingTab {
     RingPop pop[2][LB_QMAX];
 };
-/* Fills tab from the tables at d_ctab (launch_pair_table) for sets of q[0], q[1]
- * populations; synchronises stream. Returns 0, or -1 when a set's populations are not
- * in the order the layout-10 kernel is specialised on (the product rule, ascending
- * abscissae) or a copy failed. */
-int ring_tab_build(const void *d_ctab, const int q[2], RingTab *tab, void *stream);
+/* Fills tab from the tables at d_ctab (launch_pair_table) and the set constants of p;
+ * synchronises stream. Returns 0, or -1 when a set's populations are not in the order
+ * the layout-10 kernel is specialised on (the product rule, ascending abscissae) or a
+ * copy failed. */
+int ring_tab_build(const void *d_ctab, const StepParams<float> &p, RingTab *tab, void *stream);
 /* Layout 10: the row queues of one lattice. rows[] holds work items (row << 16 | kind
  * << 14 | tile; kind 0 lean, 1 edge, 2 general); queue q owns rows[desc[q].x ..
  * desc[q].x + desc[q].y); queues 0 .. nq - 1 belong to SMs (by %smid modulo nq), queue

@@ -44,6 +44,15 @@ namespace lbk {
  * odd rule); the host checks each lattice's sets against it before offering layout 10 */
 __host__ __device__ constexpr int gh_sign(int n, int i) { return (n & 1) && i == n / 2 ? 0 : (i < n / 2 ? -1 : 1); }
 
+/* a pair of deviations rounded as the storage format stores them */
+template <int ST>
+__device__ __forceinline__ float2 pair_round(float2 v)
+{
+    if constexpr (ST == 3) return __half22float2(__float22half2_rn(v));
+    else if constexpr (ST == 4) return __bfloat1622float2(__float22bfloat162_rn(v));
+    else return v;
+}
+
 /* Row kinds of the queues */
 enum : uint32_t { RING_LEAN = 0u, RING_EDGE = 1u, RING_ROW = 2u, RING_GENERAL = 3u };
 
@@ -58,17 +67,18 @@ __host__ __device__ constexpr size_t ring_unit_smem_bytes()
 /* The boundary work of a row of kind RING_ROW (set S of Q populations, the other set of
  * QT), after the population loop has stored every node of the lane's quad as an inner
  * node: the diffuse-wall fill (Sec. 3.2; num = sum over the wall-bound populations of
- * |xi.n| w d, wsgn = +1 bottom wall, -1 top wall), the copies of the row into its ghost
- * rows and of the lane's nodes into periodic ghost columns, and the mode-B rebuild of a
- * shadow row in the other set (Sec. 2.2). Loops over populations are unrolled, so every
- * constant of the velocity sets is an immediate operand. */
+ * |xi.n| w d, wsgn = +1 bottom wall, -1 top wall) with the wall row's carried moments
+ * summed again from its final values, the copies of the row into its ghost rows and of
+ * the lane's nodes into periodic ghost columns, and the mode-B rebuild of a shadow row
+ * in the other set (Sec. 2.2). Few rows take this path, so its loops stay rolled (the
+ * code stays small and in the instruction cache), with the constants read from the
+ * parameter-space table by a warp-uniform index. */
 template <int ST, int Q, int S, int QT, bool COL>
-__device__ __forceinline__ void ring_row_finish(const StepParams<float> &p, int x0, int j, uint8_t flags, float wsgn,
-                                                const float4 &num, const float (&dl)[8])
+__device__ __forceinline__ void ring_row_finish(const StepParams<float> &p, const RingTab &tab, int x0, int j,
+                                                uint8_t flags, float wsgn, const float4 &num, const float (&dl)[8])
 {
     using T = typename Store<ST>::T;
-    const SetConst<float> &c = p.set[S];
-    const SetConst<float> &ct = p.set[1 - S];
+    const RingPop *tp = tab.pop[S];
     const float rho0 = p.rho0;
     const uint32_t plane = (uint32_t)p.plane, pitch = (uint32_t)p.pitch;
     const uint32_t col = (uint32_t)(x0 + LB_GHOST);
@@ -107,47 +117,78 @@ __device__ __forceinline__ void ring_row_finish(const StepParams<float> &p, int 
         float rwd[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) rwd[k] = fmaf(rho0, kd, nm[k]) / kout;   /* rho_W - rho0 */
-#pragma unroll
+#pragma unroll 1
         for (int a = 0; a < Q; ++a) {
-            if (c.cy[a] * wsgn <= 0.0f) continue;
-            const float ew = c.cx[a] * uwx + c.cy[a] * uwy;
+            const RingPop &rp = tp[a];
+            if (rp.cy2.x * wsgn <= 0.0f) continue;
+            const float ew = rp.cx2.x * uwx + rp.cy2.x * uwy;
             const float sm1 = ew + 0.5f * (ew * ew - usw);    /* S / w - 1 */
             T e[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) e[k] = enc(fmaf(rwd[k] + rho0, sm1, rwd[k]), c.w[a], k);
+            for (int k = 0; k < 4; ++k) e[k] = enc(fmaf(rwd[k] + rho0, sm1, rwd[k]), rp.w2.x, k);
             copies(frow + (size_t)a * plane, e, true);
         }
     }
     if (nimg == 0 && !gx && !shadow) return;
-    /* copies of the populations the loop stored, and the shadow's Hermite coefficients */
-    float h[4][6];
+    /* copies of the populations the loop stored, the shadow's Hermite coefficients and,
+     * for a wall row, its carried moments summed again from its final values */
+    float h[4][6], mo[3][4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < 4; ++k) {
+        mo[0][k] = mo[1][k] = mo[2][k] = 0.0f;
 #pragma unroll
         for (int m = 0; m < 6; ++m) h[k][m] = 0.0f;
-#pragma unroll
+    }
+#pragma unroll 1
     for (int a = 0; a < Q; ++a) {
+        const RingPop &rp = tp[a];
         T *prow = frow + (size_t)a * plane;
         T raw[4];
         ldn<4>(prow + col, raw);
-        if (!(wall >= 0 && c.cy[a] * wsgn > 0.0f)) copies(prow, raw, false);
-        if (shadow) {
+        if (!(wall >= 0 && rp.cy2.x * wsgn > 0.0f)) copies(prow, raw, false);
+        if (shadow || wall >= 0) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 float d;
-                if constexpr (COL) d = decode_col<ST>(raw[k], c.winv[a], rho0, dl[k + 2]);
-                else d = decode<ST>(raw[k], c.winv[a], rho0);
-                hermite_acc(c, a, d, h[k]);
+                if constexpr (COL) d = decode_col<ST>(raw[k], rp.winv2.x, rho0, dl[k + 2]);
+                else d = decode<ST>(raw[k], rp.winv2.x, rho0);
+                if (shadow) {   /* the terms of hermite_acc, in its order */
+                    h[k][0] = fmaf(rp.w2.x, d, h[k][0]);
+                    h[k][1] = fmaf(rp.wcx2.x, d, h[k][1]);
+                    h[k][2] = fmaf(rp.wcy2.x, d, h[k][2]);
+                    h[k][3] = fmaf(rp.wxx, d, h[k][3]);
+                    h[k][4] = fmaf(rp.wxy, d, h[k][4]);
+                    h[k][5] = fmaf(rp.wyy, d, h[k][5]);
+                }
+                mo[0][k] = fmaf(rp.w2.x, d, mo[0][k]);
+                mo[1][k] = fmaf(rp.wcx2.x, d, mo[1][k]);
+                mo[2][k] = fmaf(rp.wcy2.x, d, mo[2][k]);
             }
         }
     }
-    if (!shadow) return;
-    T *const trow = static_cast<T *>(p.fout[1 - S]) + (size_t)j * pitch;
+    if (wall >= 0) {
+        float *aout = static_cast<float *>(p.aux_out) + (size_t)j * pitch + x0;
+        const size_t ap = (size_t)pitch * p.ny;
 #pragma unroll
+        for (int i = 0; i < 3; ++i)
+            __stcg(reinterpret_cast<float4 *>(aout + i * ap), make_float4(mo[i][0], mo[i][1], mo[i][2], mo[i][3]));
+    }
+    if (!shadow) return;
+    const RingPop *tq = tab.pop[1 - S];
+    T *const trow = static_cast<T *>(p.fout[1 - S]) + (size_t)j * pitch;
+#pragma unroll 1
     for (int b = 0; b < QT; ++b) {
+        const RingPop &rb = tq[b];
         T e[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) e[k] = enc(hermite_rebuild(ct, b, h[k]), ct.w[b], k);
+        for (int k = 0; k < 4; ++k) {   /* hermite_rebuild, term by term */
+            float v = fmaf(h[k][1], rb.cx2.x, h[k][0]);
+            v = fmaf(h[k][2], rb.cy2.x, v);
+            v = fmaf(h[k][3], rb.hxx, v);
+            v = fmaf(h[k][4], rb.hxy, v);
+            v = fmaf(h[k][5], rb.hyy, v);
+            e[k] = enc(v, rb.w2.x, k);
+        }
         copies(trow + (size_t)b * plane, e, true);
     }
 }
@@ -252,22 +293,29 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
         else return decode<ST>(raw, winv, rho0);
     };
 
-    /* 1. moments */
-    float2 rd[2] = {f2(0.0f), f2(0.0f)}, jx[2] = {f2(0.0f), f2(0.0f)}, jy[2] = {f2(0.0f), f2(0.0f)};
-#pragma unroll (Q == 36 ? 6 : Q)
-    for (int a = 0; a < Q; ++a) {
-        const RingPop &rp = tp[a];
-        float2 v[2];
-        pair_ld<ST>(fin + (uint32_t)a * plane + own, v[0], v[1]);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const float2 d = dec2(v[h], rp.winv2, 2 * h);
-            rd[h] = fma2(rp.w2, d, rd[h]);
-            jx[h] = fma2(rp.wcx2, d, jx[h]);
-            jy[h] = fma2(rp.wcy2, d, jy[h]);
-        }
+    /* 1. moments of the level read, carried from the step that wrote it: per node the
+     * sums sum w d, sum w xi_x d, sum w xi_y d of the stored deviations, in population
+     * order (aux_in, [3][ny][pitch]; loaded before the ring's first copies are waited
+     * for) */
+    const size_t ap = (size_t)pitch * p.ny;
+    const uint32_t m = (uint32_t)j * pitch + (uint32_t)x0;
+    float2 rd[2], jx[2], jy[2];
+    {
+        const float *ain = static_cast<const float *>(p.aux_in);
+        const float4 r4 = __ldcg(reinterpret_cast<const float4 *>(ain + m));
+        const float4 x4 = __ldcg(reinterpret_cast<const float4 *>(ain + ap + m));
+        const float4 y4 = __ldcg(reinterpret_cast<const float4 *>(ain + 2 * ap + m));
+        rd[0] = make_float2(r4.x, r4.y);
+        rd[1] = make_float2(r4.z, r4.w);
+        jx[0] = make_float2(x4.x, x4.y);
+        jx[1] = make_float2(x4.z, x4.w);
+        jy[0] = make_float2(y4.x, y4.y);
+        jy[1] = make_float2(y4.z, y4.w);
     }
     const PairNode nd = pair_node_state<FORCE>(p, rd, jx, jy);
+    /* the same sums of the values this step stores */
+#pragma unroll
+    for (int h = 0; h < 2; ++h) rd[h] = jx[h] = jy[h] = f2(0.0f);
 
     /* 2. populations: a = iy N + ix, stage a % 3 */
     auto body = [&](int a, auto sxc, auto hyc, auto stc, int b, auto bhx, auto bhy, auto bst, bool more) {
@@ -373,6 +421,19 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
         float2 dn[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) dn[h] = add2(v[h], c[h]);
+        /* carried moments: the deviations as stored (what the next step would read) */
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float2 ds;
+            if constexpr (ST == 1) ds = fma2(mul2(rp.w2, add2(f2(rho0), dn[h])), rp.winv2, nrho02);
+            else if constexpr (COL) {
+                const float2 dc = make_float2(dl[2 * h + 2], dl[2 * h + 3]);
+                ds = add2(pair_round<ST>(sub2(dn[h], dc)), dc);
+            } else ds = pair_round<ST>(dn[h]);
+            rd[h] = fma2(rp.w2, ds, rd[h]);
+            jx[h] = fma2(rp.wcx2, ds, jx[h]);
+            jy[h] = fma2(rp.wcy2, ds, jy[h]);
+        }
         T *dst = fout + (uint32_t)a * plane + own;
         if constexpr (ROW) {
             /* wall row: the wall-bound populations' |xi.n| w d, summed in population order */
@@ -460,7 +521,13 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
         }
     }
     ring_wait<0>();
-    if constexpr (ROW) ring_row_finish<ST, Q, S, QT, COL>(p, x0, j, flags, wsgn, *numslot, dl);
+    {
+        float *aout = static_cast<float *>(p.aux_out);
+        __stcg(reinterpret_cast<float4 *>(aout + m), make_float4(rd[0].x, rd[0].y, rd[1].x, rd[1].y));
+        __stcg(reinterpret_cast<float4 *>(aout + ap + m), make_float4(jx[0].x, jx[0].y, jx[1].x, jx[1].y));
+        __stcg(reinterpret_cast<float4 *>(aout + 2 * ap + m), make_float4(jy[0].x, jy[0].y, jy[1].x, jy[1].y));
+    }
+    if constexpr (ROW) ring_row_finish<ST, Q, S, QT, COL>(p, tab, x0, j, flags, wsgn, *numslot, dl);
 }
 
 /* general units (boundary work, stochastic rounding): the body of layout 9, not inlined,

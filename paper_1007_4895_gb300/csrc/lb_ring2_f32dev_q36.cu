@@ -9,7 +9,7 @@ template void launch_ring_units_store<2, 36>(const StepParams<float> &, const Ri
 }
 
 namespace lbk {
-int ring_tab_build(const void *d_ctab, const int q[2], RingTab *tab, void *stream)
+int ring_tab_build(const void *d_ctab, const StepParams<float> &p, RingTab *tab, void *stream)
 {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     PairTables *h = new PairTables;
@@ -19,13 +19,14 @@ int ring_tab_build(const void *d_ctab, const int q[2], RingTab *tab, void *strea
     auto sgn_f = [](float v) { return v > 0.0f ? 1 : (v < 0.0f ? -1 : 0); };
     auto sgn_i = [](int v) { return v > 0 ? 1 : (v < 0 ? -1 : 0); };
     for (int s = 0; s < 2 && rc == 0; ++s) {
-        const int n = q[s] == 9 ? 3 : (q[s] == 16 ? 4 : (q[s] == 36 ? 6 : 0));
+        const int qs = p.set[s].q;
+        const int n = qs == 9 ? 3 : (qs == 16 ? 4 : (qs == 36 ? 6 : 0));
         if (n == 0) rc = -1;
         for (int a = 0; a < LB_QMAX && rc == 0; ++a) {
             const PairC &pc = h->pp[s][a];
             const PairC2 &p2 = h->pp2[s][a];
             const MomC2 &pm = h->pm[s][a];
-            if (a < q[s] && (sgn_f(pc.crx) != gh_sign(n, a % n) || sgn_i(pc.ystep) != gh_sign(n, a / n))) rc = -1;
+            if (a < qs && (sgn_f(pc.crx) != gh_sign(n, a % n) || sgn_i(pc.ystep) != gh_sign(n, a / n))) rc = -1;
             RingPop &r = tab->pop[s][a];
             r.cx2 = pc.cx2;
             r.cy2 = pc.cy2;
@@ -39,7 +40,13 @@ int ring_tab_build(const void *d_ctab, const int q[2], RingTab *tab, void *strea
             r.wcy2 = pm.wcy2;
             r.kx = pc.kx;
             r.ystep = pc.ystep;
-            r.pad[0] = r.pad[1] = 0;
+            const SetConst<float> &c = p.set[s];
+            r.wxx = c.wxx[a];
+            r.wxy = c.wxy[a];
+            r.wyy = c.wyy[a];
+            r.hxx = c.hxx[a];
+            r.hxy = c.hxy[a];
+            r.hyy = c.hyy[a];
         }
     }
     delete h;
