@@ -126,7 +126,8 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-STEP_SOURCES = ("lb_internal.h", "lb_common.cuh", "lb_store.cuh", "lb_step_impl.cuh", "lb_step.cu", "lb_pair.cuh")
+STEP_SOURCES = ("lb_internal.h", "lb_common.cuh", "lb_store.cuh", "lb_step_impl.cuh", "lb_step.cu", "lb_pair.cuh",
+                "lb_ring.cuh", "lb_ring2.cuh", "lb_api.cu")
 
 
 def kernel_sha():
@@ -136,7 +137,7 @@ def kernel_sha():
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_1007_4895_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        if f in STEP_SOURCES or f.startswith(("lb_step_st_", "lb_pair_")):
+        if f in STEP_SOURCES or f.startswith(("lb_step_st_", "lb_pair_", "lb_ring_", "lb_ring2_")):
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:12]
 

@@ -121,6 +121,7 @@ __global__ void pressure_kernel(const __grid_constant__ StepParams<typename Stor
     const bool h0 = a0 < q, h1 = a1 < q;
     int img[2];
     const int nimg = row_images(p, j, img);
+    T e0 = T(0), e1 = T(0);   /* the boundary node's final populations a0, a1 */
     if (is_pressure_node(p, xb, j)) {
         R d0 = R(0), d1 = R(0), r = R(0), mx = R(0), my = R(0);
         if (h0) {
@@ -140,18 +141,18 @@ __global__ void pressure_kernel(const __grid_constant__ StepParams<typename Stor
         my = warp_sum(my);
         const R rn = rho0 + r, uxn = mx / rn, uyn = my / rn, usn = uxn * uxn + uyn * uyn;
         const R rb = p.rho_side[side];
-        auto put = [&](int a, R d) {
+        auto put = [&](int a, R d) -> T {
             const R e = c.cx[a] * uxn + c.cy[a] * uyn;
             const R dv = deq(rb - rho0, rb, e, usn) + (d - deq(r, rn, e, usn));
             const T v = enc_at<ST>(p, dv, c.w[a], xb + LB_GHOST);
             f[a * plane + xb] = v;
             for (int t = 0; t < nimg; ++t) f[a * plane + (ptrdiff_t)img[t] * p.pitch + xb] = v;
+            return v;
         };
-        if (h0) put(a0, d0);
-        if (h1) put(a1, d1);
-        /* carried moments of the node (streamed layout): its final populations summed in
+        if (h0) e0 = put(a0, d0);
+        if (h1) e1 = put(a1, d1);
+        /* carried moments of the node (layouts 4 and 10): its final populations summed in
          * population order, as the moment pass of the step kernels does */
-        const T e0 = h0 ? f[a0 * plane + xb] : T(0), e1 = h1 ? f[a1 * plane + xb] : T(0);
         R sr = R(0), sx = R(0), sy = R(0);
         for (int a = 0; a < q; ++a) {
             const T e = __shfl_sync(0xffffffffu, a < 32 ? e0 : e1, a & 31);
@@ -167,16 +168,19 @@ __global__ void pressure_kernel(const __grid_constant__ StepParams<typename Stor
             aout[ap + m] = sx;
             aout[2 * ap + m] = sy;
         }
+    } else {
+        /* a wall row: the node the step kernel stored */
+        if (h0) e0 = f[a0 * plane + xb];
+        if (h1) e1 = f[a1 * plane + xb];
     }
     /* ghost columns, and the node's second-order Hermite coefficients for a shadow */
     R hc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-    auto ghost = [&](int a) {
-        const T e = f[a * plane + xb];
+    auto ghost = [&](int a, T e) {
         for (int g = 1; g <= LB_GHOST; ++g) f[a * plane + (side == 0 ? xb - g : xb + g)] = e;
         hermite_acc(c, a, dec_at<ST>(p, e, c.winv[a], xb + LB_GHOST), hc);
     };
-    if (h0) ghost(a0);
-    if (h1) ghost(a1);
+    if (h0) ghost(a0, e0);
+    if (h1) ghost(a1, e1);
     if (flags & LB_TILE_SHADOW) {
 #pragma unroll
         for (int m = 0; m < 6; ++m) hc[m] = warp_sum(hc[m]);
