@@ -729,7 +729,7 @@ bool variant_available(const lb_ctx *c, int v)
         /* paired FP32 arithmetic: FP32 and 16-bit storage, 32-bit element offsets */
         const size_t span = std::max(c->q[0], c->q[1]) * (size_t)(c->ny + 2 * LB_GHOST_ROWS) * c->pitch;
         if (use_f64(c) || !c->d_ctab || span >= (1ull << 32)) return false;
-        if (v == 10)   /* D2Q9 with D2Q16 or D2Q36, constants checked, units listed */
+        if (v == 10)   /* D2Q9 with D2Q16 or D2Q36, constants checked, rows listed */
             return c->rtab && c->d_rctr && c->q[0] == 9 && (c->q[1] == 16 || c->q[1] == 36) && !c->rrows_h.empty();
         return v != 8 || c->border_used;
     }
@@ -768,8 +768,11 @@ int autotune_t(lb_ctx *c)
     }
     int best = 0;
     float best_ms = 1e30f;
+    /* under stochastic rounding every row of layout 10 takes layout 9's body: not offered */
+    const bool sr = c->opts.rounding == LB_ROUND_STOCHASTIC &&
+                    (c->store == LB_STORE_F16_DEV || c->store == LB_STORE_BF16_DEV);
     for (int v = 0; v < LB_NUM_VARIANTS; ++v) {
-        if (!variant_available(c, v)) continue;
+        if (!variant_available(c, v) || (v == 10 && sr)) continue;
         for (int k = 0; k < 2; ++k) launch_variant<R>(c, v, p);
         cudaEventRecord(e0, c->stream);
         for (int k = 0; k < 5; ++k) launch_variant<R>(c, v, p);
