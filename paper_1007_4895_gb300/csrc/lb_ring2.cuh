@@ -25,8 +25,12 @@
  * constants, and the per-population constants are read from kernel-parameter space
  * with a warp-uniform index. General rows run the body of layout 9, not inlined.
  *
- * The arithmetic is that of layout 9 (lb_pair.cuh), operation for operation, so the
- * two layouts give the same bits.
+ * Without a body force, the rows of the first and last tiles also do the pressure
+ * columns' update (lb_pressure.cuh, the same code as the pressure pass), so such a step
+ * needs no pressure pass.
+ *
+ * The arithmetic is that of layout 9 (lb_pair.cuh) and of the pressure pass, operation for
+ * operation, so the two layouts give the same bits.
  */
 #pragma once
 
@@ -36,6 +40,7 @@
 #include <atomic>
 #include <type_traits>
 
+#include "lb_pressure.cuh"
 #include "lb_ring.cuh"
 
 namespace lbk {
@@ -611,6 +616,14 @@ __global__ void __launch_bounds__(LB_BX *LB_BY, RING_MIN_BLOCKS)
             else ring_lean<ST, Q1, 1, 9, COL, FORCE, RING_EDGE>(p, tab, x0, j, flags, ring_smem);
         }
         __syncwarp();
+        /* the pressure columns of this row: the pressure pass's work, done here once the
+         * row's nodes are stored (the warp barrier above makes them visible to all lanes);
+         * lattices with a body force keep the pressure pass (its registers would weigh on
+         * the force kernels) */
+        if constexpr (!FORCE) {
+            if (tx == 0 && p.pressure[0]) pressure_row<ST>(p, j, 0);
+            if (tx == p.ntx - 1 && p.pressure[1]) pressure_row<ST>(p, j, 1);
+        }
     }
     /* the last warp out zeroes the counters for the next launch */
     uint32_t done = 0;
