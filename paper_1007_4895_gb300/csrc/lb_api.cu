@@ -754,6 +754,8 @@ int autotune_t(lb_ctx *c)
     uint64_t hsh = 1469598103934665603ull;
     for (uint8_t b : c->tmap) hsh = (hsh ^ b) * 1099511628211ull;
     if (c->d_dcol) hsh = (hsh ^ 0x9e3779b97f4a7c15ull) * 1099511628211ull;   /* fewer layouts available */
+    /* the rounding and the body force change which layout is fastest */
+    hsh = (hsh ^ (uint64_t)(c->opts.rounding + 2 * (c->opts.gx != 0.0 || c->opts.gy != 0.0))) * 1099511628211ull;
     TuneKey key{c->store, c->nx, c->ny, c->q[0], c->q[1], c->opts.iface, hsh};
     {
         std::lock_guard<std::mutex> g(g_tune_mu);

@@ -61,12 +61,38 @@ __device__ __forceinline__ float2 pair_round(float2 v)
 /* Row kinds of the queues */
 enum : uint32_t { RING_LEAN = 0u, RING_EDGE = 1u, RING_ROW = 2u, RING_GENERAL = 3u };
 
+/* Ring stages of layout 10 (each laid out as a stage of layout 9's ring, so that the
+ * general rows' body uses the first three) and resident blocks per SM, by measurement
+ * on the 16384 x 128 channel and the 1024 x 512 Poiseuille channel: FP32 storage four
+ * stages, two blocks of 128 registers (three stages at three blocks of 80 registers
+ * were as fast on the channel and 12 % slower on the Poiseuille lattice); 16-bit
+ * storage three stages, three blocks (a fourth stage was 4 % slower). */
+#ifndef RING10_STAGES_F32
+#define RING10_STAGES_F32 4
+#endif
+#ifndef RING10_STAGES_16
+#define RING10_STAGES_16 3
+#endif
+#ifndef RING10_BLOCKS_F32
+#define RING10_BLOCKS_F32 2
+#endif
+template <int ST>
+__host__ __device__ constexpr int ring10_stages()
+{
+    return sizeof(typename Store<ST>::T) == 4 ? RING10_STAGES_F32 : RING10_STAGES_16;
+}
+template <int ST>
+__host__ __device__ constexpr int ring10_blocks()
+{
+    return sizeof(typename Store<ST>::T) == 4 ? RING10_BLOCKS_F32 : 3;
+}
+static_assert(RING10_STAGES_F32 >= RING_STAGES && RING10_STAGES_16 >= RING_STAGES, "layout 9's body needs its stages");
 /* Dynamic shared memory of a layout-10 block: the ring, then 16 bytes per thread for the
  * wall sums of a wall row. */
 template <int ST>
 __host__ __device__ constexpr size_t ring_unit_smem_bytes()
 {
-    return ring_smem_bytes<ST>() + (size_t)LB_BX * LB_BY * sizeof(float4);
+    return ring10_stages<ST>() * ring_stage_bytes<ST>() + (size_t)LB_BX * LB_BY * sizeof(float4);
 }
 
 /* The boundary work of a row of kind RING_ROW (set S of Q populations, the other set of
@@ -215,6 +241,7 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
     constexpr int NT = LB_BX * LB_BY;
     constexpr int C4 = 4 * (int)sizeof(T), C2 = 2 * (int)sizeof(T);
     constexpr size_t STAGE = ring_stage_bytes<ST>();
+    constexpr int RS = ring10_stages<ST>();
     const RingPop *tp = tab.pop[S];
     const int tid = threadIdx.x;
     /* edge kind: nodes this lane stores one by one (pressure column, beyond nx, periodic
@@ -236,7 +263,7 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
         if (j == 0 && p.wall_diffuse[0]) wsgn = 1.0f;
         if (j == p.ny - 1 && p.wall_diffuse[1]) wsgn = -1.0f;
     }
-    float4 *const numslot = reinterpret_cast<float4 *>(ring + ring_smem_bytes<ST>()) + tid;
+    float4 *const numslot = reinterpret_cast<float4 *>(ring + RS * STAGE) + tid;
     if constexpr (ROW) *numslot = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     const T *__restrict__ fin = static_cast<const T *>(p.fin[S]);
     T *__restrict__ fout = static_cast<T *>(p.fout[S]);
@@ -253,7 +280,7 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
     }
     unsigned char *const mine4 = ring + (size_t)tid * C4;
     unsigned char *const mine2 = ring + (size_t)4 * NT * C4 + (size_t)tid * C2;
-    /* copies of population b into ring stage b % 3 (HX: xi_x != 0, HY: xi_y != 0) */
+    /* copies of population b into ring stage b % RS (HX: xi_x != 0, HY: xi_y != 0) */
     auto issue = [&](int b, auto hx, auto hy, auto stage) {
         constexpr int st = decltype(stage)::value;
         const T *pa = fin + (uint32_t)b * plane + own;
@@ -271,22 +298,18 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
             ring_cp<C2>(s2 + (size_t)NT * C2, pa + 4);
         }
     };
-    using I0 = std::integral_constant<int, 0>;
-    using I1 = std::integral_constant<int, 1>;
     using BT = std::true_type;
-    using BF = std::false_type;
-    /* populations 0 and 1 */
-    if constexpr (N == 3) {
-        issue(0, BT{}, BT{}, I0{});   /* (-, -) */
-        ring_commit();
-        issue(1, BF{}, BT{}, I1{});   /* (0, -) */
-        ring_commit();
-    } else {
-        issue(0, BT{}, BT{}, I0{});
-        ring_commit();
-        issue(1, BT{}, BT{}, I1{});
-        ring_commit();
-    }
+    /* population b, b < Q: whether xi_x and xi_y are nonzero, and its stage */
+    auto hxc = [](auto bc) { return std::bool_constant<gh_sign(N, decltype(bc)::value % N) != 0>{}; };
+    auto hyc = [](auto bc) { return std::bool_constant<gh_sign(N, decltype(bc)::value / N) != 0>{}; };
+    auto stc = [](auto bc) { return std::integral_constant<int, decltype(bc)::value % RS>{}; };
+    /* populations 0 .. RS - 2 */
+    [&]<int... B>(std::integer_sequence<int, B...>) {
+        ((issue(B, hxc(std::integral_constant<int, B>{}), hyc(std::integral_constant<int, B>{}),
+                stc(std::integral_constant<int, B>{})),
+          ring_commit()),
+         ...);
+    }(std::make_integer_sequence<int, RS - 1>{});
 
     auto dec2 = [&](float2 raw, float2 winv2, int k) -> float2 {
         if constexpr (ST == 1) return fma2(raw, winv2, nrho02);
@@ -322,12 +345,12 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
 #pragma unroll
     for (int h = 0; h < 2; ++h) rd[h] = jx[h] = jy[h] = f2(0.0f);
 
-    /* 2. populations: a = iy N + ix, stage a % 3 */
+    /* 2. populations: a = iy N + ix in stage a % RS; population a + RS - 1 is copied */
     auto body = [&](int a, auto sxc, auto hyc, auto stc, int b, auto bhx, auto bhy, auto bst, bool more) {
         constexpr int SX = decltype(sxc)::value;
         constexpr bool HY = decltype(hyc)::value;
         constexpr int st = decltype(stc)::value;
-        ring_wait<RING_STAGES - 2>();
+        ring_wait<RS - 2>();
         const RingPop &rp = tp[a];
         T own_v[4], yv[3][4], hl[2], hr[2];
         const unsigned char *s4 = mine4 + st * STAGE;
@@ -475,55 +498,29 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
         }
     };
 
-    if constexpr (N == 3) {
-        /* D2Q9, fully unrolled: (sx, sy) of a = 3 iy + ix is (ix - 1, iy - 1) */
-        using IM = std::integral_constant<int, -1>;
-        using IZ = std::integral_constant<int, 0>;
-        using IP = std::integral_constant<int, 1>;
-        using I2 = std::integral_constant<int, 2>;
-        body(0, IM{}, BT{}, I0{}, 2, BT{}, BT{}, I2{}, true);
-        body(1, IZ{}, BT{}, I1{}, 3, BT{}, BF{}, I0{}, true);
-        body(2, IP{}, BT{}, I2{}, 4, BF{}, BF{}, I1{}, true);
-        body(3, IM{}, BF{}, I0{}, 5, BT{}, BF{}, I2{}, true);
-        body(4, IZ{}, BF{}, I1{}, 6, BT{}, BT{}, I0{}, true);
-        body(5, IP{}, BF{}, I2{}, 7, BF{}, BT{}, I1{}, true);
-        body(6, IM{}, BT{}, I0{}, 8, BT{}, BT{}, I2{}, true);
-        body(7, IZ{}, BT{}, I1{}, 0, BT{}, BT{}, I0{}, false);
-        body(8, IP{}, BT{}, I2{}, 0, BT{}, BT{}, I0{}, false);
-    } else {
-        /* product sets of even n: every xi_x and xi_y nonzero, sign(xi_x) = sign by ix */
-        static_assert(Q % RING_STAGES == 0 || Q == 16, "ring stages");
-#pragma unroll (N == 6 ? 1 : N)
-        for (int iy = 0; iy < N; ++iy) {
-            const int a0 = iy * N;
-            const bool last = iy == N - 1;
-            auto sxof = [](auto ixc) { return std::integral_constant<int, gh_sign(N, decltype(ixc)::value)>{}; };
-            auto one = [&](auto ixc) {
-                constexpr int ix = decltype(ixc)::value;
-                /* stage of a = a0 + ix: a0 % 3 is 0 for n = 6; for n = 4 the loop is unrolled */
-                const int a = a0 + ix;
-                const bool more = !(last && ix + 2 >= N);
-                if constexpr (N == 6) {
-                    body(a, sxof(ixc), BT{}, std::integral_constant<int, ix % 3>{}, a + 2, BT{}, BT{},
-                         std::integral_constant<int, (ix + 2) % 3>{}, more);
-                } else {
-                    /* n = 4: iy is a compile-time constant after unrolling only in value,
-                     * so the stage comes from a runtime-uniform a; dispatch on it */
-                    const int st = a % 3;
-                    if (st == 0) body(a, sxof(ixc), BT{}, I0{}, a + 2, BT{}, BT{}, std::integral_constant<int, 2>{}, more);
-                    else if (st == 1) body(a, sxof(ixc), BT{}, I1{}, a + 2, BT{}, BT{}, I0{}, more);
-                    else body(a, sxof(ixc), BT{}, std::integral_constant<int, 2>{}, a + 2, BT{}, BT{}, I1{}, more);
-                }
-            };
-            one(std::integral_constant<int, 0>{});
-            one(std::integral_constant<int, 1>{});
-            one(std::integral_constant<int, 2>{});
-            one(std::integral_constant<int, 3>{});
-            if constexpr (N == 6) {
-                one(std::integral_constant<int, 4>{});
-                one(std::integral_constant<int, 5>{});
-            }
+    /* population A (compile-time): its sign pattern and stage, and the copy of A + RS - 1 */
+    auto one = [&](int a, auto ac) {
+        constexpr int A = decltype(ac)::value, B = A + RS - 1;
+        using IB = std::integral_constant<int, (B < Q ? B : 0)>;
+        body(a, std::integral_constant<int, gh_sign(N, A % N)>{}, hyc(ac), stc(ac), a + RS - 1, hxc(IB{}), hyc(IB{}),
+             stc(std::integral_constant<int, B>{}), a + RS - 1 < Q);
+    };
+    if constexpr (N == 6) {
+        /* D2Q36: a loop over blocks of P abscissa rows, P N populations each, so that every
+         * population's stage is the same in each pass (P N a multiple of RS) */
+        constexpr int P = (RS == 3) ? 1 : 2;
+        static_assert((P * N) % RS == 0, "D2Q36 passes");
+#pragma unroll 1
+        for (int a0 = 0; a0 < Q; a0 += P * N) {
+            [&]<int... I>(std::integer_sequence<int, I...>) {
+                (one(a0 + I, std::integral_constant<int, I>{}), ...);
+            }(std::make_integer_sequence<int, P * N>{});
         }
+    } else {
+        /* D2Q9 and D2Q16: fully unrolled */
+        [&]<int... A>(std::integer_sequence<int, A...>) {
+            (one(A, std::integral_constant<int, A>{}), ...);
+        }(std::make_integer_sequence<int, Q>{});
     }
     ring_wait<0>();
     {
@@ -556,7 +553,7 @@ __device__ __forceinline__ uint32_t ring_smid()
 
 /* Sets of D2Q9 (set 0) and Q1 = 16 or 36 populations (set 1). */
 template <int ST, bool COL, bool FORCE, int Q1>
-__global__ void __launch_bounds__(LB_BX *LB_BY, RING_MIN_BLOCKS)
+__global__ void __launch_bounds__(LB_BX *LB_BY, ring10_blocks<ST>())
     ring_unit_kernel(const __grid_constant__ StepParams<float> p, const __grid_constant__ RingTab tab,
                      const RowQueues rq)
 {
