@@ -215,11 +215,13 @@ def step_times(torch, lats, streams, reps):
     return [(i, a.elapsed_time(b)) for i, a, b in ev]
 
 
-def launches_per_step(variant, pressure):
+def launches_per_step(variant, pressure, force=False):
     """Kernels one lattice step launches: the step kernel, the edge-list kernel of the
     split layouts (2, 3; the list always holds the wall rows), and the pressure pass when
-    the lattice has pressure columns."""
-    return (2 if variant in (2, 3) else 1) + (1 if pressure else 0)
+    the lattice has pressure columns (layout 10 does those inside its kernel unless the
+    lattice has a body force)."""
+    own_pressure = variant == 10 and not force
+    return (2 if variant in (2, 3) else 1) + (1 if pressure and not own_pressure else 0)
 
 
 # ------------------------------------------------------------- oracle parts

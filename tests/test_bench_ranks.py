@@ -60,3 +60,16 @@ def test_reference_arm_prints_on_rank_zero_only(rank):
         assert line["impl"] == "reference" and line["unit"] == "MLUPS" and line["value"] > 0
     else:
         assert not lines
+
+
+def test_launch_count_per_step_of_each_layout():
+    """gpu_launches is the bench's claim: the step kernel, the edge kernel of the split
+    layouts, and the pressure pass unless layout 10 does the pressure columns itself
+    (lattices without a body force)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.launches_per_step(0, pressure=True) == 2
+    assert bench.launches_per_step(2, pressure=True) == 3
+    assert bench.launches_per_step(10, pressure=True) == 1
+    assert bench.launches_per_step(10, pressure=True, force=True) == 2
+    assert bench.launches_per_step(5, pressure=False) == 1
