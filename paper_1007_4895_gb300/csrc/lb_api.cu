@@ -118,6 +118,7 @@ struct lb_ctx {
     void *d_dcol = nullptr;         /* per-column reference density: delta per storage column (R) */
     void *d_ctab = nullptr;         /* layouts 7 / 8: per-population constant tables */
     int nsm = 0;                    /* SMs of the device */
+    bool ring_batch = false;        /* a member of a batch stepped on layout 10's bodies */
     /* layout 10: row queues (per SM and shared), their counters, and the constants
      * passed in kernel-parameter space */
     std::vector<uint32_t> rrows_h;
@@ -358,7 +359,8 @@ int finalize_level_t(lb_ctx *c, int level)
     lbk::launch_pressure<R>(c->store, p, st);
     /* carried moments of this level: read only by layouts 4 and 10 (and by the
      * autotuner, which runs while no layout is chosen yet) */
-    if (c->variant < 0 || c->variant == 4 || c->variant == 10) lbk::launch_aux<R>(c->store, p, nullptr, 0, st);
+    if (c->variant < 0 || c->variant == 4 || c->variant == 10 || c->ring_batch)
+        lbk::launch_aux<R>(c->store, p, nullptr, 0, st);
     return launch_check(c, "finalize");
 }
 
@@ -1659,6 +1661,12 @@ struct lb_batch {
     unsigned int *d_queue = nullptr;
     int threads = 256, grid = 1;
     int phase = 0;                  /* lattices' current level, relative to params [i][0] */
+    /* on layout 10's bodies: constants tables [n], work items and their range per lattice */
+    bool ring = false, force = false;
+    int q1 = 0;
+    lbk::RingTab *d_tabs = nullptr;
+    uint32_t *d_items = nullptr;
+    int2 *d_ranges = nullptr;
     int status = LB_OK;
     std::vector<void *> owned;
 };
@@ -1712,12 +1720,74 @@ int batch_upload_params(lb_batch *b)
     return LB_OK;
 }
 
+/* Work items of the ring batch (see launch_ring_batch): per lattice, runs of consecutive
+ * rows of one set and kind, at most 32 quads each, most work first; and every lattice's
+ * constants table. */
+int batch_ring_setup(lb_batch *b)
+{
+    std::vector<uint32_t> items;
+    std::vector<int2> ranges(b->n);
+    std::vector<lbk::RingTab> tabs(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        const lb_ctx *c = b->inst[i];
+        if (!c->rtab) return fail(LB_ERR_INVALID, "a batched lattice has no layout-10 constants");
+        tabs[i] = *c->rtab;
+        const bool py = c->walls[0].kind == LB_WALL_PERIODIC;
+        const int qpr = (c->nx + 3) / 4, per = 32 / qpr;
+        std::vector<std::pair<int, uint32_t>> K;
+        int j = 0;
+        while (j < c->ny) {
+            /* set | kind << 1: 0 edge (stores node by node where not plain), 1 row (ghost-row
+             * copies, wall or shadow: the row body), 2 general (such a row ending inside a
+             * quad: layout 9's body) */
+            auto key = [&](int r) {
+                const uint8_t f = c->tmap[(size_t)r * c->ntx];
+                const bool bound = (f & LB_TILE_SHADOW) || (py ? (r < 2 || r >= c->ny - 2) : (r == 0 || r == c->ny - 1));
+                const int kind = !bound ? 0 : (c->nx % 4 == 0 ? 1 : 2);
+                return (int)(f & LB_TILE_HIGH) | (kind << 1);
+            };
+            const int k0 = key(j);
+            int r = j;
+            while (r < c->ny && r - j < per && key(r) == k0) ++r;
+            const uint32_t w = (uint32_t)j | ((uint32_t)(r - j - 1) << 16) | ((uint32_t)(k0 & 1) << 21) |
+                               ((uint32_t)(k0 >> 1) << 22);
+            K.emplace_back(c->q[k0 & 1] * (r - j) * ((k0 >> 1) ? 3 : 2), w);
+            j = r;
+        }
+        std::stable_sort(K.begin(), K.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
+        ranges[i] = make_int2((int)items.size(), (int)K.size());
+        for (const auto &k : K) items.push_back(k.second);
+    }
+    b->d_tabs = static_cast<lbk::RingTab *>(batch_alloc(b, sizeof(lbk::RingTab) * b->n));
+    b->d_items = static_cast<uint32_t *>(batch_alloc(b, sizeof(uint32_t) * items.size()));
+    b->d_ranges = static_cast<int2 *>(batch_alloc(b, sizeof(int2) * b->n));
+    if (!b->d_tabs || !b->d_items || !b->d_ranges) return fail(LB_ERR_NOMEM, "device allocation failed");
+    if (cudaMemcpyAsync(b->d_tabs, tabs.data(), sizeof(lbk::RingTab) * b->n, cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(b->d_items, items.data(), sizeof(uint32_t) * items.size(), cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(b->d_ranges, ranges.data(), sizeof(int2) * b->n, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return fail(LB_ERR_CUDA, "batch item upload failed");
+    int resident = 0;
+    if (lbk::launch_ring_batch(b->store, b->q1, nullptr, nullptr, nullptr, nullptr, nullptr, b->n, 0, 0, 0, nullptr,
+                               b->force, 0, &resident, b->stream) != 0 || resident < 1)
+        return fail(LB_ERR_CUDA, "the batch kernel cannot be resident");
+    b->threads = 256;   /* the block the kernel is built for */
+    b->grid = std::min(b->n, resident);
+    return LB_OK;
+}
+
 int batch_launch(lb_batch *b, int64_t nsteps, int advance, cudaStream_t st)
 {
     if (cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned int), st) != cudaSuccess)
         return fail(LB_ERR_CUDA, "batch queue reset failed");
-    if (lbk::launch_batch(b->store, b->d_params, b->d_order, b->n, (int)nsteps, b->phase, advance, b->d_queue, b->threads,
-                          b->grid, st) != 0)
+    const int r = b->ring ? lbk::launch_ring_batch(b->store, b->q1, static_cast<const StepParams<float> *>(b->d_params),
+                                                   b->d_tabs, b->d_items, b->d_ranges, b->d_order, b->n, (int)nsteps,
+                                                   b->phase, advance, b->d_queue, b->force, b->grid, nullptr, st)
+                          : lbk::launch_batch(b->store, b->d_params, b->d_order, b->n, (int)nsteps, b->phase, advance,
+                                              b->d_queue, b->threads, b->grid, st);
+    if (r != 0)
         return fail(LB_ERR_INVALID, "bad batch block shape");
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -1780,9 +1850,19 @@ int lb_batch_create(int32_t n, const lb_grid *grids, const uint8_t *const *maps,
     b->opts = opts[0];
     b->store = opts[0].store;
     b->stream = static_cast<cudaStream_t>(opts[0].stream);
+    /* layout 10's bodies for FP32 and 16-bit storage, D2Q9 with D2Q16 or D2Q36, lattices at
+     * most one tile wide; else the one-quad batch kernel */
+    b->ring = b->store != LB_STORE_F64 && sets[0] == 9 && (sets[1] == 16 || sets[1] == 36);
+    for (int i = 0; i < n; ++i) {
+        b->ring = b->ring && grids[i].nx <= LB_TILE_X;
+        b->force = b->force || opts[i].gx != 0.0 || opts[i].gy != 0.0;
+    }
+    b->q1 = sets[1];
     for (int i = 0; i < n; ++i) {
         lb_opts o = opts[i];
-        o.variant = 0;   /* no per-lattice timing: the batch kernel does the stepping */
+        /* no per-lattice timing: the batch kernel does the stepping, with the bits of
+         * layout 9 (ring batch) or layout 0, which a lattice then takes on its own too */
+        o.variant = b->ring ? 9 : 0;
         o.stream = opts[0].stream;
         lb_ctx *c = nullptr;
         if (int e = lb_create(&grids[i], maps[i], sets, &kn[i], walls + 4 * (size_t)i, &o, &c)) {
@@ -1791,6 +1871,7 @@ int lb_batch_create(int32_t n, const lb_grid *grids, const uint8_t *const *maps,
             delete b;
             return fail(e, msg);
         }
+        c->ring_batch = b->ring;
         b->inst.push_back(c);
     }
     /* most work first */
@@ -1814,11 +1895,13 @@ int lb_batch_create(int32_t n, const lb_grid *grids, const uint8_t *const *maps,
     if (!e && cudaMemcpyAsync(b->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
         e = fail(LB_ERR_CUDA, "batch order upload failed");
     if (!e) e = b->store == LB_STORE_F64 ? batch_upload_params<double>(b) : batch_upload_params<float>(b);
-    /* block size: time each candidate on the batch without moving the state */
+    if (!e && b->ring) e = batch_ring_setup(b);
+    /* block size of the one-quad kernel: time each candidate without moving the state */
     int dev = 0, nsm = 0;
-    if (!e && (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess))
+    if (!e && !b->ring &&
+        (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess))
         e = fail(LB_ERR_CUDA, "device query failed");
-    if (!e) {
+    if (!e && !b->ring) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
@@ -1880,6 +1963,12 @@ int lb_batch_step_each(lb_batch *b, int64_t nsteps)
         for (lb_ctx *c : b->inst)
             if (int e = lb_step(c, 1)) return e;
     b->phase ^= (int)(nsteps & 1);
+    /* layout 9 carries no moments: the ring batch's are summed again */
+    if (b->ring && nsteps > 0)
+        for (lb_ctx *c : b->inst) {
+            lbk::launch_aux<float>(c->store, make_params<float>(c, c->cur, c->cur, c->t), nullptr, 0, c->stream);
+            if (int e = launch_check(c, "carried moments")) return e;
+        }
     return LB_OK;
 }
 

@@ -182,6 +182,16 @@ struct RowQueues {
     uint32_t *ctr;
     int nq;
 };
+/* Batched lattices on layout 10's bodies (FP32 and 16-bit storage, sets of 9 and q1 = 16
+ * or 36 populations, lattices at most one tile wide): params [n][2] as for launch_batch,
+ * tabs [n], items of lattice i at items[ranges[i].x ..][ranges[i].y] (first row | (rows -
+ * 1) << 16 | set << 21 | kind << 22, kind 0 edge, 1 row, 2 general), force when some
+ * lattice has a body force. grid
+ * 0: the number of resident blocks goes to *grid_out and nothing is launched. Returns 0
+ * or -1. */
+int launch_ring_batch(int store, int q1, const StepParams<float> *params, const RingTab *tabs, const uint32_t *items,
+                      const int2 *ranges, const int *order, int n, int nsteps, int base, int advance,
+                      unsigned int *queue, bool force, int grid, int *grid_out, void *stream);
 /* Layout 10 (sets of 9 and of 16 or 36 populations), at most nblocks blocks */
 void launch_ring_units(int store, const StepParams<float> &p, const RingTab &tab, const RowQueues &rq, int nblocks,
                        void *stream);

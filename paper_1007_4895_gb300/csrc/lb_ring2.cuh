@@ -117,6 +117,12 @@ __device__ __forceinline__ void ring_row_finish(const StepParams<float> &p, cons
     int img[2] = {0, 0};
     const int nimg = row_images(p, j, img);
     const bool gx = p.periodic_x && (x0 < LB_GHOST || x0 + 3 >= p.nx - LB_GHOST);
+    /* a quad whose one periodic image is a whole quad: its offset (one vector store) */
+    int img_dx = 0;
+    if (gx && (p.nx & 3) == 0) {
+        if (x0 + 3 < LB_GHOST && x0 + 3 < p.nx - LB_GHOST) img_dx = p.nx;
+        else if (x0 >= p.nx - LB_GHOST && x0 >= LB_GHOST) img_dx = -p.nx;
+    }
     const bool shadow = flags & LB_TILE_SHADOW;
     const int wall = wsgn > 0.0f ? 0 : (wsgn < 0.0f ? 1 : -1);
     auto enc = [&](float d, float w, int k) -> T {
@@ -129,7 +135,9 @@ __device__ __forceinline__ void ring_row_finish(const StepParams<float> &p, cons
         for (int t = -1; t < nimg; ++t) {
             T *r = t < 0 ? prow : prow + (ptrdiff_t)img[t] * (ptrdiff_t)pitch;
             if (t >= 0 || self) st4(r + col, e);
-            if (gx) {
+            if (img_dx != 0) {
+                st4(r + col + img_dx, e);
+            } else if (gx) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int x = x0 + k;
@@ -248,12 +256,19 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
      * ghost-column images) */
     bool valid[4] = {true, true, true, true};
     bool plain = true;
+    int img_dx = 0;   /* a whole quad whose one periodic image is a whole quad: its offset */
     if constexpr (EDGE) {
         plain = !(p.periodic_x && (x0 < LB_GHOST || x0 + 3 >= p.nx - LB_GHOST));
+        bool all = true;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             valid[k] = x0 + k < p.nx && !is_pressure_node(p, x0 + k, j);
             plain = plain && valid[k];
+            all = all && valid[k];
+        }
+        if (!plain && all && p.periodic_x && (p.nx & 3) == 0) {
+            if (x0 + 3 < LB_GHOST && x0 + 3 < p.nx - LB_GHOST) img_dx = p.nx;
+            else if (x0 >= p.nx - LB_GHOST && x0 >= LB_GHOST) img_dx = -p.nx;
         }
     }
     /* row kind: the wall of a diffuse-wall row (+1 bottom, -1 top, 0 none) and the lane's
@@ -476,14 +491,20 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
                 *numslot = n;
             }
         }
-        if (!EDGE || plain) {
+        if (!EDGE || plain || img_dx != 0) {
+            float2 e0, e1;
             if constexpr (ST == 1) {
-                pair_st<ST>(dst, mul2(rp.w2, add2(f2(rho0), dn[0])), mul2(rp.w2, add2(f2(rho0), dn[1])));
+                e0 = mul2(rp.w2, add2(f2(rho0), dn[0]));
+                e1 = mul2(rp.w2, add2(f2(rho0), dn[1]));
             } else if constexpr (COL) {
-                pair_st<ST>(dst, sub2(dn[0], make_float2(dl[2], dl[3])), sub2(dn[1], make_float2(dl[4], dl[5])));
+                e0 = sub2(dn[0], make_float2(dl[2], dl[3]));
+                e1 = sub2(dn[1], make_float2(dl[4], dl[5]));
             } else {
-                pair_st<ST>(dst, dn[0], dn[1]);
+                e0 = dn[0];
+                e1 = dn[1];
             }
+            pair_st<ST>(dst, e0, e1);
+            if (EDGE && img_dx != 0) pair_st<ST>(dst + img_dx, e0, e1);
         } else {
             const float dv[4] = {dn[0].x, dn[0].y, dn[1].x, dn[1].y};
             T *prow = dst - col;
@@ -658,6 +679,116 @@ void ring_unit_launch(const StepParams<float> &p, const RingTab &tab, const RowQ
     const int grid = std::min(nb, nblocks);
     if (grid <= 0) return;
     ring_unit_kernel<ST, COL, FORCE, Q1><<<grid, LB_BX * LB_BY, smem, st>>>(p, tab, rq);
+}
+
+/* ------------------------------------------------------------------------------
+ * Batched lattices on layout 10's bodies. A block takes a lattice from the queue (most
+ * work first), copies its two launch parameter sets (level n -> n+1 and back) and its
+ * constants table into shared memory after its ring, and advances it nsteps steps with a
+ * block barrier between steps. Within a step the block's warps take the lattice's items
+ * (host-built, most work first): up to 32 quads of consecutive rows of one set, lane l on
+ * quad l % qpr of row l / qpr (qpr quads per row). Rows without walls, ghost-row copies or
+ * shadows run the edge body (its stores do the periodic ghost columns), the others the
+ * row body (its epilogue does them), or layout 9's body where a row ends inside a quad:
+ * the same bits as layout 9 stepping each lattice alone.
+ * Item word: first row | (rows - 1) << 16 | set << 21 | kind << 22 (0 edge, 1 row, 2
+ * general).
+ * ---------------------------------------------------------------------------- */
+constexpr size_t ring_batch_params_bytes() { return (2 * sizeof(StepParams<float>) + 15) / 16 * 16; }
+template <int ST>
+__host__ __device__ constexpr size_t ring_batch_smem_bytes()
+{
+    return ring_unit_smem_bytes<ST>() + ring_batch_params_bytes() + sizeof(RingTab);
+}
+
+template <int ST, bool FORCE, int Q1>
+__global__ void __launch_bounds__(LB_BX *LB_BY, ring10_blocks<ST>())
+    ring_batch_kernel(const StepParams<float> *__restrict__ params, const RingTab *__restrict__ tabs,
+                      const uint32_t *__restrict__ items, const int2 *__restrict__ ranges,
+                      const int *__restrict__ order, int n, int nsteps, int base, int advance, unsigned int *queue)
+{
+    extern __shared__ __align__(16) unsigned char ring_smem[];
+    static_assert(ring_unit_smem_bytes<ST>() % 16 == 0 && sizeof(RingTab) % 16 == 0 && sizeof(StepParams<float>) % 4 == 0,
+                  "aligned copies");
+    StepParams<float> *sp = reinterpret_cast<StepParams<float> *>(ring_smem + ring_unit_smem_bytes<ST>());
+    RingTab *tab = reinterpret_cast<RingTab *>(ring_smem + ring_unit_smem_bytes<ST>() + ring_batch_params_bytes());
+    __shared__ int inst_sh;
+    __shared__ unsigned int icount;
+    const uint32_t lane = threadIdx.x & 31u;
+    for (;;) {
+        __syncthreads();   /* every thread is done with the previous lattice */
+        if (threadIdx.x == 0) {
+            const unsigned k = atomicAdd(queue, 1u);
+            inst_sh = k < (unsigned)n ? order[k] : -1;
+        }
+        __syncthreads();
+        const int inst = inst_sh;
+        if (inst < 0) return;
+        {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(params + 2 * (size_t)inst);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(sp);
+            for (int k = threadIdx.x; k < (int)(2 * sizeof(StepParams<float>) / 4); k += blockDim.x) dst[k] = src[k];
+            const uint4 *ts = reinterpret_cast<const uint4 *>(tabs + inst);
+            uint4 *td = reinterpret_cast<uint4 *>(tab);
+            for (int k = threadIdx.x; k < (int)(sizeof(RingTab) / 16); k += blockDim.x) td[k] = ts[k];
+        }
+        const int2 rg = ranges[inst];
+        for (int st = 0; st < nsteps; ++st) {
+            if (threadIdx.x == 0) icount = 0u;
+            __syncthreads();   /* parameters in place; the previous step done by every warp */
+            const StepParams<float> &p = sp[advance ? ((base + st) & 1) : base];
+            const int qpr = (p.nx + 3) / 4;
+            for (;;) {
+                unsigned it = 0;
+                if (lane == 0) it = atomicAdd(&icount, 1u);
+                it = __shfl_sync(0xffffffffu, it, 0);
+                if (it >= (unsigned)rg.y) break;
+                const uint32_t w = items[rg.x + it];
+                const int j0 = (int)(w & 0xffffu), nr = (int)((w >> 16) & 31u) + 1;
+                const int s = (int)((w >> 21) & 1u);
+                const int r = (int)lane / qpr, x0 = ((int)lane - r * qpr) * 4;
+                if (r < nr && x0 < p.nx) {
+                    const int j = j0 + r;
+                    const uint8_t flags = p.tmap[(size_t)j * p.ntx + x0 / LB_TILE_X];
+                    const uint32_t kind = (w >> 22) & 3u;
+                    if (kind == 2u) ring_general<ST, false, FORCE>(p, s, flags, x0, j, ring_smem);
+                    else if (kind == 1u && s == 0) ring_lean<ST, 9, 0, Q1, false, FORCE, RING_ROW>(p, *tab, x0, j, flags, ring_smem);
+                    else if (kind == 1u) ring_lean<ST, Q1, 1, 9, false, FORCE, RING_ROW>(p, *tab, x0, j, flags, ring_smem);
+                    else if (s == 0) ring_lean<ST, 9, 0, Q1, false, FORCE, RING_EDGE>(p, *tab, x0, j, flags, ring_smem);
+                    else ring_lean<ST, Q1, 1, 9, false, FORCE, RING_EDGE>(p, *tab, x0, j, flags, ring_smem);
+                }
+                __syncwarp();
+            }
+            __syncthreads();   /* the step is complete for the whole lattice */
+        }
+    }
+}
+
+/* force: some lattice of the batch has a body force (the force terms then run for every
+ * lattice; with g = 0 they add exact zeros). grid 0: the resident blocks of the device
+ * are returned in *grid_out and nothing is launched. */
+template <int ST, int Q1>
+int launch_ring_batch_store(const StepParams<float> *params, const RingTab *tabs, const uint32_t *items,
+                            const int2 *ranges, const int *order, int n, int nsteps, int base, int advance,
+                            unsigned int *queue, bool force, int grid, int *grid_out, void *stream)
+{
+    constexpr size_t smem = ring_batch_smem_bytes<ST>();
+    auto kern = force ? ring_batch_kernel<ST, true, Q1> : ring_batch_kernel<ST, false, Q1>;
+    if (grid < 1) {
+        cudaFuncSetAttribute(ring_batch_kernel<ST, true, Q1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(ring_batch_kernel<ST, false, Q1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0, dev = 0, nsm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LB_BX * LB_BY, smem) != cudaSuccess ||
+            cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+        *grid_out = per_sm * nsm;
+        return per_sm > 0 ? 0 : -1;
+    }
+    kern<<<grid, LB_BX * LB_BY, smem, static_cast<cudaStream_t>(stream)>>>(params, tabs, items, ranges, order, n,
+                                                                        nsteps, base, advance, queue);
+    return 0;
 }
 
 /* layout 10 for one storage format and high-order set size */

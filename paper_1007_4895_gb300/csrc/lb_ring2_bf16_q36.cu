@@ -6,4 +6,7 @@
 namespace lbk {
 template void launch_ring_units_store<4, 36>(const StepParams<float> &, const RingTab &, const RowQueues &,
                                               int, void *);
+template int launch_ring_batch_store<4, 36>(const StepParams<float> *, const RingTab *, const uint32_t *,
+                                                 const int2 *, const int *, int, int, int, int, unsigned int *, bool,
+                                                 int, int *, void *);
 }

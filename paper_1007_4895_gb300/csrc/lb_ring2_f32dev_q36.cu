@@ -6,6 +6,9 @@
 namespace lbk {
 template void launch_ring_units_store<2, 36>(const StepParams<float> &, const RingTab &, const RowQueues &,
                                               int, void *);
+template int launch_ring_batch_store<2, 36>(const StepParams<float> *, const RingTab *, const uint32_t *,
+                                                 const int2 *, const int *, int, int, int, int, unsigned int *, bool,
+                                                 int, int *, void *);
 }
 
 namespace lbk {

@@ -26,6 +26,10 @@ void launch_ring_store(const StepParams<float> &p, void *stream);
 template <int ST, int Q1>
 void launch_ring_units_store(const StepParams<float> &p, const RingTab &tab, const RowQueues &rq, int nblocks,
                              void *stream);
+template <int ST, int Q1>
+int launch_ring_batch_store(const StepParams<float> *params, const RingTab *tabs, const uint32_t *items,
+                            const int2 *ranges, const int *order, int n, int nsteps, int base, int advance,
+                            unsigned int *queue, bool force, int grid, int *grid_out, void *stream);
 
 /* ---------------------------------------------------------------- mode A -- */
 
@@ -266,6 +270,24 @@ void launch_ring_units(int store, const StepParams<float> &p, const RingTab &tab
         case 4: (q36 ? launch_ring_units_store<4, 36> : launch_ring_units_store<4, 16>)(p, tab, rq, nblocks, stream); break;
         default: break;
     }
+}
+
+int launch_ring_batch(int store, int q1, const StepParams<float> *params, const RingTab *tabs, const uint32_t *items,
+                      const int2 *ranges, const int *order, int n, int nsteps, int base, int advance,
+                      unsigned int *queue, bool force, int grid, int *grid_out, void *stream)
+{
+    const bool q36 = q1 == 36;
+    if (!q36 && q1 != 16) return -1;
+#define LB_RB(ST) (q36 ? launch_ring_batch_store<ST, 36> : launch_ring_batch_store<ST, 16>)( \
+        params, tabs, items, ranges, order, n, nsteps, base, advance, queue, force, grid, grid_out, stream)
+    switch (store) {
+        case 1: return LB_RB(1);
+        case 2: return LB_RB(2);
+        case 3: return LB_RB(3);
+        case 4: return LB_RB(4);
+        default: return -1;
+    }
+#undef LB_RB
 }
 
 void launch_pair(int store, const StepParams<float> &p, void *stream)

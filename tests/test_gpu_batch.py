@@ -1,8 +1,9 @@
 """Batched channels (lb_batch_*): many independent lattices advanced by one persistent
-launch. The batch does the one-quad layout's arithmetic in the same order, so every
-lattice must equal the same lattice stepped on its own, bit for bit; a few lattices are
-also checked against the FP64 oracle, and the full 512-channel sweep against mass
-conservation and the oracle on sampled channels."""
+launch. In FP64 the batch does the one-quad layout's arithmetic, in FP32 and 16-bit
+storage layout 10's bodies (the bits of layout 9), so every lattice must equal the same
+lattice stepped on its own with that layout, bit for bit; a few lattices are also
+checked against the FP64 oracle, and the full 512-channel sweep against the oracle on
+sampled channels."""
 import numpy as np
 import pytest
 
@@ -15,14 +16,15 @@ def _pops(lat):
     return [lat.populations(s) for s in (0, 1)]
 
 
-@pytest.mark.parametrize("store", ["f64", "f32_dev"])
+@pytest.mark.parametrize("store", ["f64", "f32_dev", "bf16_dev"])
 def test_batch_equals_lattices_stepped_alone(store):
     import paper_1007_4895_gb300 as lb
     ws = batched_instances(n=24, seed=7)
     b = lb.Batch(ws, store=store)
     b.step(31)
     for i in (0, 5, 11, 23):
-        alone = lb.Lattice.from_workload(batched_instances(n=24, seed=7)[i], store=store, variant=0)
+        alone = lb.Lattice.from_workload(batched_instances(n=24, seed=7)[i], store=store,
+                                         variant=0 if store == "f64" else 9)
         alone.step(31)
         got, ref = _pops(b.lattice(i)), _pops(alone)
         for s in (0, 1):
