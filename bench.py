@@ -285,6 +285,34 @@ def steady_accuracy(lb, forms):
     return out
 
 
+def batched_sweep(lb, torch, store, steps=500):
+    """The 512 seeded channels of the batched configuration (8 x 16..256 nodes, Couette
+    and Poiseuille, Kn 0.01..1) advanced together by one persistent launch per call:
+    MLUPS over `steps` steps (CUDA events on the batch's stream), with the algorithmic
+    bytes of those steps against the measured HBM rate."""
+    from lbinputs import batched_instances
+    ws = batched_instances()
+    b = lb.Batch(ws, store=store)
+    b.step(20)
+    b.sync()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    b.step(steps)
+    e1.record(s)
+    b.sync()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nodes = sum(w.nx * w.ny for w in ws)
+    nbytes = sum(algorithmic_bytes(b.lattice(i).effective_map(), b.lattice(i).sets, store) for i in range(len(ws)))
+    peak, _ = measured_peak_hbm()
+    out = {"value": nodes * steps / (ms / 1e3) / 1e6, "unit": "MLUPS", "lattices": len(ws), "nodes": nodes,
+           "steps": steps, "ms": ms, "roofline_frac": nbytes * steps / (ms / 1e3) / 1e9 / peak,
+           "kernel": b.info()}
+    b.close()
+    return out
+
+
 def config5_study(lb, torch, nx=16384, ny=128, steps=2000, every=200, samples=100000, threshold=3e-4, epochs=20):
     """Learned interface placement on the long channel (the headline geometry at CFL 0.38,
     where an all-high-order map is stable): an all-D2Q36 run gives the features and the
@@ -542,6 +570,7 @@ def main():
         forms["accuracy_cases"] = (f"the headline lattice after {PARITY_STEPS} steps against the FP64 oracle; "
                                    "steady Poiseuille 4x64, Kn 0.1, 6000 steps; max relative errors")
         forms["learned_placement"] = config5_study(lb, torch)
+        forms["batched_512"] = batched_sweep(lb, torch, args.store)
 
     # secondary: three force-driven 1024 x 512 channels (Kn 0.02 / 0.1 / 0.5), one stream
     # each, stepped together
