@@ -1725,39 +1725,75 @@ int batch_upload_params(lb_batch *b)
  * constants table. */
 int batch_ring_setup(lb_batch *b)
 {
-    std::vector<uint32_t> items;
+    /* items (two words each, longest first per lattice), then the row lists they index */
+    struct Item {
+        int cost;
+        uint32_t meta;
+        std::vector<uint32_t> rows;
+    };
+    std::vector<std::vector<Item>> all(b->n);
     std::vector<int2> ranges(b->n);
     std::vector<lbk::RingTab> tabs(b->n);
+    size_t nitems = 0, nrows = 0;
     for (int i = 0; i < b->n; ++i) {
         const lb_ctx *c = b->inst[i];
         if (!c->rtab) return fail(LB_ERR_INVALID, "a batched lattice has no layout-10 constants");
         tabs[i] = *c->rtab;
         const bool py = c->walls[0].kind == LB_WALL_PERIODIC;
         const int qpr = (c->nx + 3) / 4, per = 32 / qpr;
-        std::vector<std::pair<int, uint32_t>> K;
+        /* set | kind << 1: 0 edge (stores node by node where not plain), 1 row (ghost-row
+         * copies, wall or shadow: the row body), 2 general (such a row ending inside a
+         * quad: layout 9's body) */
+        auto key = [&](int r) {
+            const uint8_t f = c->tmap[(size_t)r * c->ntx];
+            const bool bound = (f & LB_TILE_SHADOW) || (py ? (r < 2 || r >= c->ny - 2) : (r == 0 || r == c->ny - 1));
+            const int kind = !bound ? 0 : (c->nx % 4 == 0 ? 1 : 2);
+            return (int)(f & LB_TILE_HIGH) | (kind << 1);
+        };
+        /* a lane's time is its chain of populations (the row body's epilogue adds to it),
+         * nearly whatever the item's number of rows: that is the cost */
+        auto add = [&](int k, std::vector<uint32_t> &rows) {
+            const int kind = k >> 1;
+            const int cost = c->q[k & 1] * (kind == 0 ? 5 : (kind == 1 ? 7 : 9)) * 64 + (int)rows.size();
+            all[i].push_back({cost, (uint32_t)(rows.size() - 1) | ((uint32_t)(k & 1) << 5) | ((uint32_t)kind << 6), rows});
+            rows.clear();
+        };
+        std::vector<uint32_t> pend[2];   /* row-body rows of each set, merged across the lattice */
+        std::vector<uint32_t> run;
         int j = 0;
         while (j < c->ny) {
-            /* set | kind << 1: 0 edge (stores node by node where not plain), 1 row (ghost-row
-             * copies, wall or shadow: the row body), 2 general (such a row ending inside a
-             * quad: layout 9's body) */
-            auto key = [&](int r) {
-                const uint8_t f = c->tmap[(size_t)r * c->ntx];
-                const bool bound = (f & LB_TILE_SHADOW) || (py ? (r < 2 || r >= c->ny - 2) : (r == 0 || r == c->ny - 1));
-                const int kind = !bound ? 0 : (c->nx % 4 == 0 ? 1 : 2);
-                return (int)(f & LB_TILE_HIGH) | (kind << 1);
-            };
             const int k0 = key(j);
             int r = j;
             while (r < c->ny && r - j < per && key(r) == k0) ++r;
-            const uint32_t w = (uint32_t)j | ((uint32_t)(r - j - 1) << 16) | ((uint32_t)(k0 & 1) << 21) |
-                               ((uint32_t)(k0 >> 1) << 22);
-            K.emplace_back(c->q[k0 & 1] * (r - j) * ((k0 >> 1) ? 3 : 2), w);
+            if ((k0 >> 1) == 1) {
+                for (int t = j; t < r; ++t) {
+                    pend[k0 & 1].push_back((uint32_t)t);
+                    if ((int)pend[k0 & 1].size() == per) add(k0, pend[k0 & 1]);
+                }
+            } else {
+                for (int t = j; t < r; ++t) run.push_back((uint32_t)t);
+                add(k0, run);
+            }
             j = r;
         }
-        std::stable_sort(K.begin(), K.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
-        ranges[i] = make_int2((int)items.size(), (int)K.size());
-        for (const auto &k : K) items.push_back(k.second);
+        for (int s = 0; s < 2; ++s)
+            if (!pend[s].empty()) add(s | 2, pend[s]);
+        std::stable_sort(all[i].begin(), all[i].end(), [](const Item &x, const Item &y) { return x.cost > y.cost; });
+        ranges[i] = make_int2((int)nitems, (int)all[i].size());
+        nitems += all[i].size();
+        for (const Item &it : all[i]) nrows += it.rows.size();
     }
+    if (2 * nitems + nrows > 0xffffffffull) return fail(LB_ERR_INVALID, "batch item list too large");
+    std::vector<uint32_t> items(2 * nitems);
+    items.reserve(2 * nitems + nrows);
+    size_t k = 0;
+    for (int i = 0; i < b->n; ++i)
+        for (const Item &it : all[i]) {
+            items[2 * k] = (uint32_t)items.size();
+            items[2 * k + 1] = it.meta;
+            items.insert(items.end(), it.rows.begin(), it.rows.end());
+            ++k;
+        }
     b->d_tabs = static_cast<lbk::RingTab *>(batch_alloc(b, sizeof(lbk::RingTab) * b->n));
     b->d_items = static_cast<uint32_t *>(batch_alloc(b, sizeof(uint32_t) * items.size()));
     b->d_ranges = static_cast<int2 *>(batch_alloc(b, sizeof(int2) * b->n));

@@ -59,7 +59,7 @@ __device__ __forceinline__ float2 pair_round(float2 v)
 }
 
 /* Row kinds of the queues */
-enum : uint32_t { RING_LEAN = 0u, RING_EDGE = 1u, RING_ROW = 2u, RING_GENERAL = 3u };
+enum : uint32_t { RING_LEAN = 0u, RING_EDGE = 1u, RING_ROW = 2u, RING_GENERAL = 3u, RING_BATCH = 4u };
 
 /* Ring stages of layout 10 (each laid out as a stage of layout 9's ring, so that the
  * general rows' body uses the first three) and resident blocks per SM, by measurement
@@ -106,7 +106,8 @@ __host__ __device__ constexpr size_t ring_unit_smem_bytes()
  * parameter-space table by a warp-uniform index. */
 template <int ST, int Q, int S, int QT, bool COL>
 __device__ __forceinline__ void ring_row_finish(const StepParams<float> &p, const RingTab &tab, int x0, int j,
-                                                uint8_t flags, float wsgn, const float4 &num, const float (&dl)[8])
+                                                uint8_t flags, float wsgn, const float4 &num, const float (&dl)[8],
+                                                bool noimg)
 {
     using T = typename Store<ST>::T;
     const RingPop *tp = tab.pop[S];
@@ -116,7 +117,7 @@ __device__ __forceinline__ void ring_row_finish(const StepParams<float> &p, cons
     T *const frow = static_cast<T *>(p.fout[S]) + (size_t)j * pitch;   /* row j of plane 0, column 0 - LB_GHOST */
     int img[2] = {0, 0};
     const int nimg = row_images(p, j, img);
-    const bool gx = p.periodic_x && (x0 < LB_GHOST || x0 + 3 >= p.nx - LB_GHOST);
+    const bool gx = !noimg && p.periodic_x && (x0 < LB_GHOST || x0 + 3 >= p.nx - LB_GHOST);
     /* a quad whose one periodic image is a whole quad: its offset (one vector store) */
     int img_dx = 0;
     if (gx && (p.nx & 3) == 0) {
@@ -178,30 +179,39 @@ __device__ __forceinline__ void ring_row_finish(const StepParams<float> &p, cons
 #pragma unroll
         for (int m = 0; m < 6; ++m) h[k][m] = 0.0f;
     }
+    /* four populations' quads loaded together (the stores of copies() go to other rows
+     * and columns, never to a quad still to be read), then taken in population order */
 #pragma unroll 1
-    for (int a = 0; a < Q; ++a) {
-        const RingPop &rp = tp[a];
-        T *prow = frow + (size_t)a * plane;
-        T raw[4];
-        ldn<4>(prow + col, raw);
-        if (!(wall >= 0 && rp.cy2.x * wsgn > 0.0f)) copies(prow, raw, false);
-        if (shadow || wall >= 0) {
+    for (int a0 = 0; a0 < Q; a0 += 4) {
+        T raw4[4][4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float d;
-                if constexpr (COL) d = decode_col<ST>(raw[k], rp.winv2.x, rho0, dl[k + 2]);
-                else d = decode<ST>(raw[k], rp.winv2.x, rho0);
-                if (shadow) {   /* the terms of hermite_acc, in its order */
-                    h[k][0] = fmaf(rp.w2.x, d, h[k][0]);
-                    h[k][1] = fmaf(rp.wcx2.x, d, h[k][1]);
-                    h[k][2] = fmaf(rp.wcy2.x, d, h[k][2]);
-                    h[k][3] = fmaf(rp.wxx, d, h[k][3]);
-                    h[k][4] = fmaf(rp.wxy, d, h[k][4]);
-                    h[k][5] = fmaf(rp.wyy, d, h[k][5]);
+        for (int i = 0; i < 4; ++i)
+            if (a0 + i < Q) ldn<4>(frow + (size_t)(a0 + i) * plane + col, raw4[i]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int a = a0 + i;
+            if (a >= Q) break;
+            const RingPop &rp = tp[a];
+            const T(&raw)[4] = raw4[i];
+            if (!(wall >= 0 && rp.cy2.x * wsgn > 0.0f)) copies(frow + (size_t)a * plane, raw, false);
+            if (shadow || wall >= 0) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float d;
+                    if constexpr (COL) d = decode_col<ST>(raw[k], rp.winv2.x, rho0, dl[k + 2]);
+                    else d = decode<ST>(raw[k], rp.winv2.x, rho0);
+                    if (shadow) {   /* the terms of hermite_acc, in its order */
+                        h[k][0] = fmaf(rp.w2.x, d, h[k][0]);
+                        h[k][1] = fmaf(rp.wcx2.x, d, h[k][1]);
+                        h[k][2] = fmaf(rp.wcy2.x, d, h[k][2]);
+                        h[k][3] = fmaf(rp.wxx, d, h[k][3]);
+                        h[k][4] = fmaf(rp.wxy, d, h[k][4]);
+                        h[k][5] = fmaf(rp.wyy, d, h[k][5]);
+                    }
+                    mo[0][k] = fmaf(rp.w2.x, d, mo[0][k]);
+                    mo[1][k] = fmaf(rp.wcx2.x, d, mo[1][k]);
+                    mo[2][k] = fmaf(rp.wcy2.x, d, mo[2][k]);
                 }
-                mo[0][k] = fmaf(rp.w2.x, d, mo[0][k]);
-                mo[1][k] = fmaf(rp.wcx2.x, d, mo[1][k]);
-                mo[2][k] = fmaf(rp.wcy2.x, d, mo[2][k]);
             }
         }
     }
@@ -240,9 +250,13 @@ __device__ __forceinline__ void ring_row_finish(const StepParams<float> &p, cons
  * columns). */
 template <int ST, int Q, int S, int QT, bool COL, bool FORCE, uint32_t KIND>
 __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const RingTab &tab, int x0, int j,
-                                          uint8_t flags, unsigned char *ring)
+                                          uint8_t flags, unsigned char *ring, int xmode = 0, bool rowk = true)
 {
-    constexpr bool ROW = KIND == RING_ROW;
+    /* RING_BATCH: the edge and row kinds of an x-periodic lattice of whole quads in one
+     * body, with its halos read inside the row and no ghost-column images (xmode 3), the
+     * row work run where `rowk` says so: a batch's steps then run two bodies, not four */
+    constexpr bool MIX = KIND == RING_BATCH;
+    constexpr bool ROW = KIND == RING_ROW || MIX;
     constexpr bool EDGE = KIND == RING_EDGE;   /* lanes store node by node */
     using T = typename Store<ST>::T;
     constexpr int N = Q == 9 ? 3 : (Q == 16 ? 4 : 6);
@@ -255,8 +269,15 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
     /* edge kind: nodes this lane stores one by one (pressure column, beyond nx, periodic
      * ghost-column images) */
     bool valid[4] = {true, true, true, true};
-    bool plain = true;
+    bool plain = true, allv = true;
     int img_dx = 0;   /* a whole quad whose one periodic image is a whole quad: its offset */
+    /* xmode (edge and row kinds of an x-periodic lattice whose width is a whole number of
+     * quads): bit 0, the x halos of the row's end quads are read from its other end, not
+     * from the ghost columns; bit 1, no periodic ghost-column images are written. Within
+     * a launch of several steps only the last writes them: the others' are never read. */
+    const bool wrapx = (EDGE || ROW) && (xmode & 1) != 0, noimg = (EDGE || ROW) && (xmode & 2) != 0;
+    const int hlo = (wrapx && x0 == 0) ? p.nx - 2 : -2;
+    const int hro = (wrapx && x0 + 4 == p.nx) ? 4 - p.nx : 4;
     if constexpr (EDGE) {
         plain = !(p.periodic_x && (x0 < LB_GHOST || x0 + 3 >= p.nx - LB_GHOST));
         bool all = true;
@@ -266,6 +287,7 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
             plain = plain && valid[k];
             all = all && valid[k];
         }
+        allv = all;
         if (!plain && all && p.periodic_x && (p.nx & 3) == 0) {
             if (x0 + 3 < LB_GHOST && x0 + 3 < p.nx - LB_GHOST) img_dx = p.nx;
             else if (x0 >= p.nx - LB_GHOST && x0 >= LB_GHOST) img_dx = -p.nx;
@@ -309,8 +331,8 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
             ring_cp<C4>(s4 + (size_t)3 * NT * C4, pa + ys);
         }
         if constexpr (decltype(hx)::value) {
-            ring_cp<C2>(s2, pa - 2);
-            ring_cp<C2>(s2 + (size_t)NT * C2, pa + 4);
+            ring_cp<C2>(s2, pa + hlo);
+            ring_cp<C2>(s2 + (size_t)NT * C2, pa + hro);
         }
     };
     using BT = std::true_type;
@@ -491,7 +513,7 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
                 *numslot = n;
             }
         }
-        if (!EDGE || plain || img_dx != 0) {
+        if (!EDGE || plain || img_dx != 0 || (noimg && allv)) {
             float2 e0, e1;
             if constexpr (ST == 1) {
                 e0 = mul2(rp.w2, add2(f2(rho0), dn[0]));
@@ -504,7 +526,7 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
                 e1 = dn[1];
             }
             pair_st<ST>(dst, e0, e1);
-            if (EDGE && img_dx != 0) pair_st<ST>(dst + img_dx, e0, e1);
+            if (EDGE && img_dx != 0 && !noimg) pair_st<ST>(dst + img_dx, e0, e1);
         } else {
             const float dv[4] = {dn[0].x, dn[0].y, dn[1].x, dn[1].y};
             T *prow = dst - col;
@@ -550,7 +572,9 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
         __stcg(reinterpret_cast<float4 *>(aout + ap + m), make_float4(jx[0].x, jx[0].y, jx[1].x, jx[1].y));
         __stcg(reinterpret_cast<float4 *>(aout + 2 * ap + m), make_float4(jy[0].x, jy[0].y, jy[1].x, jy[1].y));
     }
-    if constexpr (ROW) ring_row_finish<ST, Q, S, QT, COL>(p, tab, x0, j, flags, wsgn, *numslot, dl);
+    if constexpr (ROW) {
+        if (!MIX || rowk) ring_row_finish<ST, Q, S, QT, COL>(p, tab, x0, j, flags, wsgn, *numslot, dl, noimg);
+    }
 }
 
 /* general units (boundary work, stochastic rounding): the body of layout 9, not inlined,
@@ -686,13 +710,15 @@ void ring_unit_launch(const StepParams<float> &p, const RingTab &tab, const RowQ
  * work first), copies its two launch parameter sets (level n -> n+1 and back) and its
  * constants table into shared memory after its ring, and advances it nsteps steps with a
  * block barrier between steps. Within a step the block's warps take the lattice's items
- * (host-built, most work first): up to 32 quads of consecutive rows of one set, lane l on
- * quad l % qpr of row l / qpr (qpr quads per row). Rows without walls, ghost-row copies or
- * shadows run the edge body (its stores do the periodic ghost columns), the others the
- * row body (its epilogue does them), or layout 9's body where a row ends inside a quad:
- * the same bits as layout 9 stepping each lattice alone.
- * Item word: first row | (rows - 1) << 16 | set << 21 | kind << 22 (0 edge, 1 row, 2
- * general).
+ * (host-built, longest first): up to 32 quads of rows of one set and kind, lane l on quad
+ * l % qpr of the item's row l / qpr (qpr quads per row). Rows without walls, ghost-row
+ * copies or shadows run the edge body (its stores do the periodic ghost columns), the
+ * others the row body (its epilogue does them), or layout 9's body where a row ends inside
+ * a quad: the same bits as layout 9 stepping each lattice alone. The rows of a row-body
+ * item need not be adjacent (a lattice's wall and shadow rows of one set share one item:
+ * a lane's time is its population chain, whatever the number of rows).
+ * Item: two words, the index in `items` of its row list (one word per row) and
+ * (rows - 1) | set << 5 | kind << 6 (0 edge, 1 row, 2 general).
  * ---------------------------------------------------------------------------- */
 constexpr size_t ring_batch_params_bytes() { return (2 * sizeof(StepParams<float>) + 15) / 16 * 16; }
 template <int ST>
@@ -738,24 +764,29 @@ __global__ void __launch_bounds__(LB_BX *LB_BY, ring10_blocks<ST>())
             __syncthreads();   /* parameters in place; the previous step done by every warp */
             const StepParams<float> &p = sp[advance ? ((base + st) & 1) : base];
             const int qpr = (p.nx + 3) / 4;
+            /* x-periodic lattices of whole quads: halos read inside the row, ghost-column
+             * images written by the launch's last step only */
+            const int xm = (p.periodic_x && (p.nx & 3) == 0) ? (st + 1 < nsteps ? 3 : 1) : 0;
             for (;;) {
                 unsigned it = 0;
                 if (lane == 0) it = atomicAdd(&icount, 1u);
                 it = __shfl_sync(0xffffffffu, it, 0);
                 if (it >= (unsigned)rg.y) break;
-                const uint32_t w = items[rg.x + it];
-                const int j0 = (int)(w & 0xffffu), nr = (int)((w >> 16) & 31u) + 1;
-                const int s = (int)((w >> 21) & 1u);
+                const uint2 w = reinterpret_cast<const uint2 *>(items)[rg.x + it];
+                const int nr = (int)(w.y & 31u) + 1, s = (int)((w.y >> 5) & 1u);
                 const int r = (int)lane / qpr, x0 = ((int)lane - r * qpr) * 4;
                 if (r < nr && x0 < p.nx) {
-                    const int j = j0 + r;
+                    const int j = (int)items[w.x + (uint32_t)r];
                     const uint8_t flags = p.tmap[(size_t)j * p.ntx + x0 / LB_TILE_X];
-                    const uint32_t kind = (w >> 22) & 3u;
-                    if (kind == 2u) ring_general<ST, false, FORCE>(p, s, flags, x0, j, ring_smem);
-                    else if (kind == 1u && s == 0) ring_lean<ST, 9, 0, Q1, false, FORCE, RING_ROW>(p, *tab, x0, j, flags, ring_smem);
-                    else if (kind == 1u) ring_lean<ST, Q1, 1, 9, false, FORCE, RING_ROW>(p, *tab, x0, j, flags, ring_smem);
-                    else if (s == 0) ring_lean<ST, 9, 0, Q1, false, FORCE, RING_EDGE>(p, *tab, x0, j, flags, ring_smem);
-                    else ring_lean<ST, Q1, 1, 9, false, FORCE, RING_EDGE>(p, *tab, x0, j, flags, ring_smem);
+                    const uint32_t kind = (w.y >> 6) & 3u;
+                    if (xm == 3) {
+                        if (s == 0) ring_lean<ST, 9, 0, Q1, false, FORCE, RING_BATCH>(p, *tab, x0, j, flags, ring_smem, xm, kind == 1u);
+                        else ring_lean<ST, Q1, 1, 9, false, FORCE, RING_BATCH>(p, *tab, x0, j, flags, ring_smem, xm, kind == 1u);
+                    } else if (kind == 2u) ring_general<ST, false, FORCE>(p, s, flags, x0, j, ring_smem);
+                    else if (kind == 1u && s == 0) ring_lean<ST, 9, 0, Q1, false, FORCE, RING_ROW>(p, *tab, x0, j, flags, ring_smem, xm);
+                    else if (kind == 1u) ring_lean<ST, Q1, 1, 9, false, FORCE, RING_ROW>(p, *tab, x0, j, flags, ring_smem, xm);
+                    else if (s == 0) ring_lean<ST, 9, 0, Q1, false, FORCE, RING_EDGE>(p, *tab, x0, j, flags, ring_smem, xm);
+                    else ring_lean<ST, Q1, 1, 9, false, FORCE, RING_EDGE>(p, *tab, x0, j, flags, ring_smem, xm);
                 }
                 __syncwarp();
             }
