@@ -104,7 +104,7 @@ __host__ __device__ constexpr size_t ring_unit_smem_bytes()
  * in the other set (Sec. 2.2). Few rows take this path, so its loops stay rolled (the
  * code stays small and in the instruction cache), with the constants read from the
  * parameter-space table by a warp-uniform index. */
-template <int ST, int Q, int S, int QT, bool COL>
+template <int ST, int Q, int S, int QT, bool COL, int G>
 __device__ __forceinline__ void ring_row_finish(const StepParams<float> &p, const RingTab &tab, int x0, int j,
                                                 uint8_t flags, float wsgn, const float4 &num, const float (&dl)[8],
                                                 bool noimg)
@@ -179,16 +179,17 @@ __device__ __forceinline__ void ring_row_finish(const StepParams<float> &p, cons
 #pragma unroll
         for (int m = 0; m < 6; ++m) h[k][m] = 0.0f;
     }
-    /* four populations' quads loaded together (the stores of copies() go to other rows
-     * and columns, never to a quad still to be read), then taken in population order */
+    /* G populations' quads loaded together (the stores of copies() go to other rows and
+     * columns, never to a quad still to be read), then taken in population order; G > 1
+     * only where the registers allow it */
 #pragma unroll 1
-    for (int a0 = 0; a0 < Q; a0 += 4) {
-        T raw4[4][4];
+    for (int a0 = 0; a0 < Q; a0 += G) {
+        T raw4[G][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < G; ++i)
             if (a0 + i < Q) ldn<4>(frow + (size_t)(a0 + i) * plane + col, raw4[i]);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < G; ++i) {
             const int a = a0 + i;
             if (a >= Q) break;
             const RingPop &rp = tp[a];
@@ -573,7 +574,7 @@ __device__ __forceinline__ void ring_lean(const StepParams<float> &p, const Ring
         __stcg(reinterpret_cast<float4 *>(aout + 2 * ap + m), make_float4(jy[0].x, jy[0].y, jy[1].x, jy[1].y));
     }
     if constexpr (ROW) {
-        if (!MIX || rowk) ring_row_finish<ST, Q, S, QT, COL>(p, tab, x0, j, flags, wsgn, *numslot, dl, noimg);
+        if (!MIX || rowk) ring_row_finish<ST, Q, S, QT, COL, MIX ? 4 : 1>(p, tab, x0, j, flags, wsgn, *numslot, dl, noimg);
     }
 }
 
@@ -727,8 +728,11 @@ __host__ __device__ constexpr size_t ring_batch_smem_bytes()
     return ring_unit_smem_bytes<ST>() + ring_batch_params_bytes() + sizeof(RingTab);
 }
 
+/* Two blocks of 128 registers per SM for every storage: the batch's mixed body spills
+ * heavily under the 80 registers of three 16-bit blocks (BF16, 512 channels: 6970 MLUPS
+ * with two blocks against 5320 with three) */
 template <int ST, bool FORCE, int Q1>
-__global__ void __launch_bounds__(LB_BX *LB_BY, ring10_blocks<ST>())
+__global__ void __launch_bounds__(LB_BX *LB_BY, 2)
     ring_batch_kernel(const StepParams<float> *__restrict__ params, const RingTab *__restrict__ tabs,
                       const uint32_t *__restrict__ items, const int2 *__restrict__ ranges,
                       const int *__restrict__ order, int n, int nsteps, int base, int advance, unsigned int *queue)
