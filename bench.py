@@ -55,8 +55,9 @@ def parse():
     ap.add_argument("--variant", type=int, default=-1, help="step-kernel layout (-1: autotune)")
     ap.add_argument("--no-forms", action="store_true", help="skip the other storage forms")
     ap.add_argument("--no-secondary", action="store_true", help="skip the three-channel secondary workload")
-    ap.add_argument("--profile", default=None, choices=["long_channel", "poiseuille", "stream_box"],
-                    help="build one lattice, advance it --steps steps, exit (for ncu)")
+    ap.add_argument("--profile", default=None, choices=["long_channel", "poiseuille", "stream_box", "batched"],
+                    help="build one lattice (or the 512-channel batch: a 20-step launch, then one of --steps "
+                         "steps), advance it --steps steps, exit (for ncu)")
     return ap.parse_args()
 
 
@@ -432,6 +433,16 @@ def profile_only(args):
     import torch
 
     import paper_1007_4895_gb300 as lb
+    if args.profile == "batched":
+        from lbinputs import batched_instances
+        b = lb.Batch(batched_instances(), store=args.store)
+        b.step(20)
+        b.step(args.steps)
+        b.sync()
+        torch.cuda.synchronize()
+        print(args.profile, args.store, b.info())
+        b.close()
+        return
     if args.profile == "stream_box":
         periodic = {s: {"kind": "periodic"} for s in ("bottom", "top", "left", "right")}
         lat = lb.Lattice(2048, 1024, np.zeros((1024, 2048), np.uint8), kn_ref=0.002, rho_ref=1.0, walls=periodic,
