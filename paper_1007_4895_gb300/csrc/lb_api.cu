@@ -1758,7 +1758,9 @@ int batch_ring_setup(lb_batch *b)
             all[i].push_back({cost, (uint32_t)(rows.size() - 1) | ((uint32_t)(k & 1) << 5) | ((uint32_t)kind << 6), rows});
             rows.clear();
         };
-        std::vector<uint32_t> pend[2];   /* row-body rows of each set, merged across the lattice */
+        /* row-body rows of each set, merged across the lattice: wall (and periodic image)
+         * rows apart from shadow rows, so that no lane's epilogue waits on the other's */
+        std::vector<uint32_t> pend[2][2];
         std::vector<uint32_t> run;
         int j = 0;
         while (j < c->ny) {
@@ -1767,8 +1769,10 @@ int batch_ring_setup(lb_batch *b)
             while (r < c->ny && r - j < per && key(r) == k0) ++r;
             if ((k0 >> 1) == 1) {
                 for (int t = j; t < r; ++t) {
-                    pend[k0 & 1].push_back((uint32_t)t);
-                    if ((int)pend[k0 & 1].size() == per) add(k0, pend[k0 & 1]);
+                    const bool edge_row = py ? (t < 2 || t >= c->ny - 2) : (t == 0 || t == c->ny - 1);
+                    std::vector<uint32_t> &pl = pend[k0 & 1][edge_row ? 0 : 1];
+                    pl.push_back((uint32_t)t);
+                    if ((int)pl.size() == per) add(k0, pl);
                 }
             } else {
                 for (int t = j; t < r; ++t) run.push_back((uint32_t)t);
@@ -1777,7 +1781,8 @@ int batch_ring_setup(lb_batch *b)
             j = r;
         }
         for (int s = 0; s < 2; ++s)
-            if (!pend[s].empty()) add(s | 2, pend[s]);
+            for (int t = 0; t < 2; ++t)
+                if (!pend[s][t].empty()) add(s | 2, pend[s][t]);
         std::stable_sort(all[i].begin(), all[i].end(), [](const Item &x, const Item &y) { return x.cost > y.cost; });
         ranges[i] = make_int2((int)nitems, (int)all[i].size());
         nitems += all[i].size();

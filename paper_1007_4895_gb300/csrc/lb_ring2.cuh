@@ -716,8 +716,8 @@ void ring_unit_launch(const StepParams<float> &p, const RingTab &tab, const RowQ
  * copies or shadows run the edge body (its stores do the periodic ghost columns), the
  * others the row body (its epilogue does them), or layout 9's body where a row ends inside
  * a quad: the same bits as layout 9 stepping each lattice alone. The rows of a row-body
- * item need not be adjacent (a lattice's wall and shadow rows of one set share one item:
- * a lane's time is its population chain, whatever the number of rows).
+ * item need not be adjacent (a lattice's wall rows of one set share one item, its shadow
+ * rows another: a lane's time is its population chain, whatever the number of rows).
  * Item: two words, the index in `items` of its row list (one word per row) and
  * (rows - 1) | set << 5 | kind << 6 (0 edge, 1 row, 2 general).
  * ---------------------------------------------------------------------------- */
