@@ -582,6 +582,7 @@ def main():
                                    "steady Poiseuille 4x64, Kn 0.1, 6000 steps; max relative errors")
         forms["learned_placement"] = config5_study(lb, torch)
         forms["batched_512"] = batched_sweep(lb, torch, args.store)
+        forms["batched_512_bf16_dev"] = batched_sweep(lb, torch, "bf16_dev")
 
     # secondary: three force-driven 1024 x 512 channels (Kn 0.02 / 0.1 / 0.5), one stream
     # each, stepped together
