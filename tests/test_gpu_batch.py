@@ -49,6 +49,26 @@ def test_per_lattice_launches_and_graph_replays_equal_batch_steps():
                 assert np.array_equal(ra[s], ro[s]), i
 
 
+@pytest.mark.parametrize("store", ["f32_dev", "bf16_dev"])
+def test_per_lattice_steps_after_a_batch_launch_read_its_ghost_columns(store):
+    """Inside a launch of several steps the batch reads the halos of an x-periodic
+    lattice's end quads from the other end of the row and writes the periodic
+    ghost-column images only at the launch's last step. Per-lattice launches read the
+    ghost columns, so batch launches followed by per-lattice steps must give the bits of
+    per-lattice steps throughout."""
+    import paper_1007_4895_gb300 as lb
+    a = lb.Batch(batched_instances(n=16, seed=5), store=store)
+    c = lb.Batch(batched_instances(n=16, seed=5), store=store)
+    a.step(9)
+    a.step_each(3)
+    a.step(5)
+    c.step_each(17)
+    for i in range(16):
+        ra, rc = _pops(a.lattice(i)), _pops(c.lattice(i))
+        for s in (0, 1):
+            assert np.array_equal(ra[s], rc[s]), (store, i, s)
+
+
 def test_stepping_one_lattice_alone_is_refused():
     import paper_1007_4895_gb300 as lb
     b = lb.Batch(batched_instances(n=4, seed=1), store="f32_dev")
